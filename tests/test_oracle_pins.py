@@ -1,0 +1,255 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test starts from an independent definition (a direct sum, a closed form, a
+different quadrature of the same integral, an invariant) so that a dropped term, a
+wrong sign or index, or a transposed operand in the oracle fails at least one of them.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import exact as E
+from oracle import grid as G
+from paper_1608_08009_gb300 import workloads as W
+
+
+def _mesh(g):
+    return np.meshgrid(g.v, g.v, g.v, indexing="ij")
+
+
+@pytest.fixture(scope="module")
+def grid32():
+    return O.make_grid(32, 8.0, M=64, dirs_kind=2)
+
+
+# --- transforms (Eqs. FU / FC) --------------------------------------------------------
+
+def test_forward_matches_direct_sum():
+    g = O.make_grid(4, 2.5, M=4)
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal((4, 4, 4))
+    fh = O.forward(f, g, zero_nyquist=False)
+    VX, VY, VZ = _mesh(g)
+    direct = np.zeros((4, 4, 4), complex)
+    for a in range(4):
+        for b in range(4):
+            for c in range(4):
+                xi = (g.xi[a], g.xi[b], g.xi[c])
+                direct[a, b, c] = np.sum(f * np.exp(-1j * (xi[0] * VX + xi[1] * VY + xi[2] * VZ))) / 64
+    assert np.max(np.abs(fh - direct)) < 1e-14
+    back = O.inverse(fh, g)
+    assert np.max(np.abs(back - f)) < 1e-13
+
+
+def test_single_mode_coefficients():
+    g = O.make_grid(8, 3.0, M=4)
+    VX, VY, VZ = _mesh(g)
+    kx, ky, kz = 1, -2, 3
+    f = np.cos(g.xi[kx] * VX + g.xi[ky % 8] * VY + g.xi[kz] * VZ)
+    fh = O.forward(f, g)
+    expect = np.zeros((8, 8, 8), complex)
+    expect[kx, ky % 8, kz] = 0.5
+    expect[-kx % 8, -ky % 8, -kz % 8] = 0.5
+    assert np.max(np.abs(fh - expect)) < 1e-15
+
+
+# --- kernel functions (Sec. 3.3, decoupling formula) ------------------------------------
+
+def test_phi_printed_closed_form_equals_integral():
+    R = 3.7
+    s = np.linspace(0.0, 9.0, 91)
+    assert np.max(np.abs(G.phi_hs(s, R) - E.phi_quadrature(s, R))) < 1e-11 * R * R
+
+
+def test_psi_is_disk_transform_and_printed_psi_is_not():
+    R = 2.9
+    s = np.linspace(0.0, 6.0, 25)
+    quad = E.psi_quadrature(s, R)
+    assert np.max(np.abs(G.psi_hs(s, R) - quad)) < 1e-10 * R * R
+    assert np.max(np.abs(G.psi_printed(s, R) - quad)) > 0.1 * R * R
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_direction_weights(kind):
+    e, w = G.directions(64, kind)
+    assert np.allclose(np.linalg.norm(e, axis=1), 1.0, atol=1e-15)
+    tol = 0.01 if kind == 0 else 1e-13
+    assert abs(w.sum() - 2 * math.pi) < tol * 2 * math.pi
+    if kind == 2:
+        # exact for low-degree spherical polynomials on the half sphere
+        assert abs(np.sum(w * e[:, 2] ** 2) - 2 * math.pi / 3) < 1e-13
+        assert abs(np.sum(w * e[:, 0] ** 2 * e[:, 1] ** 2) - 2 * math.pi / 15) < 1e-13
+
+
+def test_kernel_l0_closed_form():
+    """K(0, m) -> B_F(0, m) = Btilde 4 pi^2 R^2 (1 - cos R|xi|)/|xi|^2 (Eq. FKM)."""
+    g = O.make_grid(16, 6.0, M=256, dirs_kind=2)
+    n = g.n
+    K0m = np.einsum("i,i,ix->x", g.w, g.alpha.reshape(g.M_eff, n)[:, 0], g.alphap.reshape(g.M_eff, n))
+    Km0 = np.einsum("i,ix,i->x", g.w, g.alpha.reshape(g.M_eff, n), g.alphap.reshape(g.M_eff, n)[:, 0])
+    KX, KY, KZ = np.meshgrid(g.xi, g.xi, g.xi, indexing="ij")
+    xn = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2).ravel()
+    exact = E.carleman_kernel_l0(xn, g.R, 4.0)
+    sel = xn * g.R < 12.0
+    scale = exact[0]
+    assert abs(K0m[0] - exact[0]) < 1e-12 * scale
+    assert np.max(np.abs(K0m[sel] - exact[sel])) < 1e-5 * scale
+    assert np.max(np.abs(Km0[sel] - exact[sel])) < 1e-5 * scale
+    # the printed psi gives a different kernel
+    e, w = G.directions(256, 2)
+    printed = np.array([np.sum(w * 4.0 * g.R ** 2 * G.psi_printed(
+        np.sqrt(np.maximum(xv ** 2 - (xv * e[:, 2]) ** 2, 0.0)), g.R)) for xv in [1.0, 2.0]])
+    assert np.max(np.abs(printed - E.carleman_kernel_l0(np.array([1.0, 2.0]), g.R, 4.0))) > 0.05 * scale
+
+
+# --- the operator --------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,L,M", [(8, 5.0, 16), (12, 6.0, 16)])
+def test_fast_equals_wrapped_spectral_sum(N, L, M):
+    g = O.make_grid(N, L, M=M, dirs_kind=0)
+    f = W.two_maxwellians(2, N, L, seed=11)
+    Qf = O.collide(f, g, project=False)
+    Qb = O.collide_brute_force(f, g)
+    assert np.linalg.norm(Qf - Qb) / np.linalg.norm(Qf) < 1e-13
+
+
+def test_mass_is_conserved_exactly():
+    g = O.make_grid(16, 6.0, M=32, dirs_kind=1)
+    f = W.two_maxwellians(3, 16, 6.0, seed=5)
+    Q = O.collide(f, g, project=False)
+    U = O.moments(Q, g)
+    A = O.moments(np.abs(Q), g)
+    assert np.all(np.abs(U[:, 0]) < 1e-13 * A[:, 0])
+
+
+def test_projection():
+    g = O.make_grid(16, 6.0, M=32, dirs_kind=0)
+    f = W.two_maxwellians(2, 16, 6.0, seed=9)
+    Q = O.collide(f, g, project=True)
+    U = O.moments(Q, g)
+    A = O.moments(np.abs(Q), g)
+    assert np.all(np.abs(U) < 1e-13 * A[:, :1].max())
+    assert np.max(np.abs(O.project_Q(Q, g) - Q)) < 1e-14 * np.abs(Q).max()
+    Ut = O.moments(f, g) * 1.01
+    fp = O.project_f(f, Ut, g)
+    assert np.max(np.abs(O.moments(fp, g) - Ut)) < 1e-13 * np.abs(Ut).max()
+
+
+def test_maxwellian_is_equilibrium_spectrally():
+    errs = []
+    for N in (16, 24, 32):
+        g = O.make_grid(N, 8.0, M=64, dirs_kind=2)
+        VX, VY, VZ = _mesh(g)
+        M1 = E.maxwellian(VX, VY, VZ, 1.3, np.array([0.2, -0.1, 0.05]), 1.0)
+        Qp, Lo = O.operator.gain_loss(M1, g)
+        errs.append(np.linalg.norm(Qp - M1 * Lo) / np.linalg.norm(Qp))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-4
+
+
+def test_loss_is_hard_sphere_collision_frequency(grid32):
+    g = grid32
+    VX, VY, VZ = _mesh(g)
+    u = np.array([0.1, 0.0, -0.2])
+    M1 = E.maxwellian(VX, VY, VZ, 0.8, u, 0.9)
+    _, Lo = O.operator.gain_loss(M1, g)
+    V = np.stack([VX, VY, VZ], axis=-1)
+    nu = E.hs_collision_frequency(V, 0.8, u, 0.9)
+    sel = np.linalg.norm(V, axis=-1) < 1.5
+    assert np.max(np.abs(Lo[sel] - nu[sel]) / nu[sel]) < 1e-5
+
+
+def test_direct_quadrature_of_boltzmann_integral(grid32):
+    g = grid32
+    gs = [(0.6, np.array([0.5, 0.3, -0.2]), 0.4), (0.4, np.array([-0.6, -0.2, 0.3]), 0.3)]
+    VX, VY, VZ = _mesh(g)
+    f = sum(E.maxwellian(VX, VY, VZ, r, u, T) for r, u, T in gs)
+    Q = O.collide(f, g, project=False)
+    qmax = np.abs(Q).max()
+    for idx in [(16, 16, 16), (18, 17, 16), (15, 14, 17)]:
+        vv = np.array([g.v[idx[0]], g.v[idx[1]], g.v[idx[2]]])
+        qd = E.boltzmann_direct(vv, gs, r_max=6.0, nr=32, nt=14, npp=28)
+        assert abs(Q[idx] - qd) < 3e-4 * qmax, (idx, Q[idx], qd)
+
+
+def test_classical_spectral_sum_converges_to_fast():
+    """Eq. (CF1)/(KM) (no direction quadrature) against the Carleman fast form.
+
+    The two truncations agree with the Boltzmann integral only on B(S) and for
+    resolved data; at N = 8 no datum is both resolved and inside B(S) (S is 1.8 grid
+    steps), so this is a convergence check from N = 16 to N = 24 at fixed data.
+    """
+    rel = []
+    for N in (16, 24):
+        g = O.make_grid(N, 5.0, M=64, dirs_kind=2)
+        VX, VY, VZ = _mesh(g)
+        f = E.maxwellian(VX, VY, VZ, 1.0, np.array([0.25, 0.0, 0.0]), 0.2) + \
+            E.maxwellian(VX, VY, VZ, 0.7, np.array([-0.25, 0.1, 0.0]), 0.16)
+        Qc = E.collide_classical(f, g, R_c=g.R)
+        Qf = O.collide(f, g, project=False)
+        assert abs(Qc.sum()) < 1e-12 * np.abs(Qc).sum()          # classical sum is mass conserving
+        rel.append(np.linalg.norm(Qc - Qf) / np.linalg.norm(Qf))
+    assert rel[1] < 0.3 and rel[1] < rel[0] / 3.0, rel
+
+
+def test_bkw_solution_moments():
+    for K in (0.6, 0.75, 0.95):
+        g = O.make_grid(32, 8.0, M=4)
+        VX, VY, VZ = _mesh(g)
+        f = E.bkw_3d(VX, VY, VZ, E.bkw_t0_for_K(K))
+        U = O.moments(f, g)
+        assert abs(U[0] - 1.0) < 1e-10 and abs(U[4] - 1.5) < 1e-10
+        assert f.min() > -1e-15
+
+
+def test_bkw_residual_maxwell_molecules():
+    """Q(f_BKW(t)) = d f_BKW / dt for gamma = 0 through the rank-r radial expansion."""
+    g = O.make_grid(24, 7.0, gamma=0.0, C_gamma=1.0 / (4.0 * math.pi), M=36, dirs_kind=2, rank=16)
+    VX, VY, VZ = _mesh(g)
+    t0 = E.bkw_t0_for_K(0.7)
+    f = E.bkw_3d(VX, VY, VZ, t0)
+    dfdt = E.bkw_3d_dt(VX, VY, VZ, t0)
+    Q = O.collide(f, g, project=False)
+    assert np.linalg.norm(Q - dfdt) / np.linalg.norm(dfdt) < 1e-3
+
+
+# --- exact structural properties ----------------------------------------------------------
+
+def test_grid_shift_equivariance():
+    g = O.make_grid(16, 6.0, M=16, dirs_kind=1)
+    f = W.two_maxwellians(1, 16, 6.0, seed=21)[0]
+    s = (1, 3, -2)
+    Q = O.collide(f, g, project=False)
+    Qs = O.collide(np.roll(f, s, axis=(0, 1, 2)), g, project=False)
+    assert np.max(np.abs(Qs - np.roll(Q, s, axis=(0, 1, 2)))) < 1e-13 * np.abs(Q).max()
+
+
+def test_bilinearity_and_reflection():
+    g = O.make_grid(16, 6.0, M=16, dirs_kind=0)
+    f = W.two_maxwellians(1, 16, 6.0, seed=23)[0]
+    Q = O.collide(f, g, project=False)
+    assert np.max(np.abs(O.collide(2.5 * f, g, project=False) - 6.25 * Q)) < 1e-13 * np.abs(Q).max()
+    # v -> -v maps index j to (N - j) mod N
+    ref = lambda a: np.roll(a[::-1, ::-1, ::-1], 1, axis=(0, 1, 2))
+    Qr = O.collide(ref(f), g, project=False)
+    assert np.max(np.abs(Qr - ref(Q))) < 1e-13 * np.abs(Q).max()
+
+
+def test_relax_conserves_and_heun_is_second_order():
+    g = O.make_grid(16, 6.0, M=16, dirs_kind=0)
+    f0 = W.two_maxwellians(1, 16, 6.0, seed=3)[0]
+    U0 = O.moments(f0, g)
+    T = 0.02      # collision frequency ~60 here: dt * nu must stay below ~1 for stability
+    ref = O.relax(f0, g, T / 32, 32, rk_order=2)
+    e1, e2 = [], []
+    for steps in (2, 4):
+        a = O.relax(f0, g, T / steps, steps, rk_order=1)
+        b = O.relax(f0, g, T / steps, steps, rk_order=2)
+        assert np.max(np.abs(O.moments(b, g) - U0)) < 1e-13 * np.abs(U0).max()
+        e1.append(np.linalg.norm(a - ref))
+        e2.append(np.linalg.norm(b - ref))
+    assert 1.6 < e1[0] / e1[1] < 2.6
+    assert 3.0 < e2[0] / e2[1] < 5.5
