@@ -186,6 +186,18 @@ def btilde(gamma: float, C_gamma: float, r1, r2):
     return 4.0 * C_gamma * (np.asarray(r1) ** 2 + np.asarray(r2) ** 2) ** (0.5 * (gamma - 1.0))
 
 
+def _perp_norm(KX, KY, KZ, e):
+    """|Pi_{e-perp} xi| = |xi x e| for a unit vector e (Sec. 3.3, argument of psi).
+
+    The cross product is used instead of sqrt(|xi|^2 - (xi . e)^2), which loses all
+    accuracy when xi is nearly parallel to e.
+    """
+    cx = KY * e[2] - KZ * e[1]
+    cy = KZ * e[0] - KX * e[2]
+    cz = KX * e[1] - KY * e[0]
+    return np.sqrt(cx * cx + cy * cy + cz * cz)
+
+
 def kernel_tables(N, L, e, w_dir, gamma=1.0, C_gamma=1.0, R=None, rank=None, inner_nodes=None):
     """alpha_i(k), alpha'_i(k), weights w_i and D(k) on the full N^3 mode set.
 
@@ -207,7 +219,6 @@ def kernel_tables(N, L, e, w_dir, gamma=1.0, C_gamma=1.0, R=None, rank=None, inn
         inner_nodes = 128
     xi = np.pi * wave_numbers(N) / L
     KX, KY, KZ = np.meshgrid(xi, xi, xi, indexing="ij")
-    K2 = KX * KX + KY * KY + KZ * KZ
     M = e.shape[0]
     Meff = M * rank
     alpha = np.empty((Meff, N, N, N))
@@ -219,7 +230,7 @@ def kernel_tables(N, L, e, w_dir, gamma=1.0, C_gamma=1.0, R=None, rank=None, inn
         bt = 4.0 * C_gamma
         for j in range(M):
             s = KX * e[j, 0] + KY * e[j, 1] + KZ * e[j, 2]
-            perp = np.sqrt(np.maximum(K2 - s * s, 0.0))
+            perp = _perp_norm(KX, KY, KZ, e[j])
             alpha[j] = bt * phi_hs(s, R)
             alphap[j] = psi_hs(perp, R)
     else:
@@ -227,7 +238,7 @@ def kernel_tables(N, L, e, w_dir, gamma=1.0, C_gamma=1.0, R=None, rank=None, inn
         rq, uq = gauss_legendre(inner_nodes, 0.0, R)
         for j in range(M):
             s = KX * e[j, 0] + KY * e[j, 1] + KZ * e[j, 2]
-            perp = np.sqrt(np.maximum(K2 - s * s, 0.0))
+            perp = _perp_norm(KX, KY, KZ, e[j])
             j0 = special.j0(rq[:, None] * perp.reshape(1, -1))  # [inner, n]
             for r in range(rank):
                 alpha[j * rank + r] = 2.0 * u[r] * rho[r] * np.cos(rho[r] * s)
