@@ -1,0 +1,163 @@
+/*
+ * boltz.h -- C ABI of libboltz: fast spectral evaluation of the Boltzmann collision
+ * operator Q(f, f) for the variable-hard-sphere kernel on an N^3 periodised velocity
+ * grid, computed independently in every spatial cell, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the fast spectral scheme of Dimarco, Loubere, Narski and Rey,
+ * "An efficient numerical method for solving the Boltzmann equation in
+ * multidimensions" (arxiv 1608.08009), Sec. 3.3 (Carleman representation, separated
+ * angular quadrature), Sec. 3.2 (L2 conservation projection, Eq. minim1) and Sec. 3.1
+ * (collision step f <- f + dt Q, Eq. f_coll), organised per cell as in Sec. 4.2: one
+ * forward transform of f, then for every quadrature direction the kernel coefficients
+ * and inverse transforms, then the gather into Q.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Layout.     A batch of cells is stored cell after cell; one cell is f[x][y][z] with
+ *              z fastest, N^3 values, value (i, j, k) taken at velocity
+ *              (-L + i dv, -L + j dv, -L + k dv), dv = 2L/N.  Q has the layout and the
+ *              element type of f.  Moments are U[c] = (rho, rho u_x, rho u_y, rho u_z, E)
+ *              = sum_v (1, v_x, v_y, v_z, |v|^2/2) f(v) dv^3, float64.
+ *  Memory.     Every f / Q / U pointer is a device pointer the caller allocated and
+ *              owns; the library never frees it.  The grid object owns its tables
+ *              (host and device copies) until boltz_destroy_grid.
+ *  Streams.    `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *              stream).  Every compute call is asynchronous on that stream.
+ *  Errors.     Argument errors are returned synchronously and leave the stream
+ *              untouched.  Conditions found on the device (non-finite results) are
+ *              OR-ed into a device status word that boltz_stream_status() reads.  No call
+ *              aborts, traps or waits without bound.  boltz_last_error() gives a
+ *              thread-local message for the last failing call of the calling thread.
+ *  Devices.    A grid is bound to the device that was current when it was created;
+ *              calls must be made with that device current.
+ */
+#ifndef BOLTZ_H
+#define BOLTZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BOLTZ_OK = 0,
+  BOLTZ_EINVAL = 1,        /* bad argument (null pointer, size, unsupported value)      */
+  BOLTZ_ENOMEM = 2,        /* host or device allocation failed                          */
+  BOLTZ_ECUDA = 3,         /* a CUDA runtime call failed (message in boltz_last_error)  */
+  BOLTZ_EUNSUPPORTED = 4,  /* valid request this build has no kernel for (e.g. N, prec)  */
+  BOLTZ_ENONFINITE = 5,    /* device status: a NaN or Inf was produced                  */
+  BOLTZ_ETIMEOUT = 6       /* device status: a bounded wait gave up (not used yet)      */
+} boltz_status;
+
+/* Arithmetic of the transforms and angular products (the hot loop).  Moments, the
+ * conservation projection and the f <- f + dt Q update are float64 in every mode. */
+typedef enum {
+  BOLTZ_FP64 = 0,          /* float64 register FFTs on CUDA cores (the plain form)      */
+  BOLTZ_FP32_FFT = 1,      /* float32 register FFTs on CUDA cores, float32 tables       */
+  BOLTZ_TF32_DFT = 2,      /* reserved: tensor-core dense DFT contractions              */
+  BOLTZ_3XBF16_DFT = 3,    /* reserved                                                  */
+  BOLTZ_3XTF32_DFT = 4     /* reserved                                                  */
+} boltz_precision;
+
+/* Options of boltz_create_grid.  Pass NULL for all defaults; boltz_default_opts()
+ * fills the defaults so that single fields can be changed. */
+typedef struct {
+  int dirs_kind;     /* half-sphere direction set (Sec. 3.3 quadrature), default 0:
+                        0 = product grid, midpoints in theta and varphi, weights
+                            (pi/A1)(pi/A2) sin(theta)  (the paper's uniform grids)
+                        1 = spherical Fibonacci points, weights 2 pi / M
+                        2 = Gauss-Legendre in cos(theta) x midpoints in varphi       */
+  int dirs_a1;       /* A1 of the product grids (must divide M); <= 0: smallest divisor
+                        of M that is >= sqrt(M) (M = 64 -> 8 x 8)                     */
+  double R_trunc;    /* Carleman ball radius R; <= 0: R = 2 S with S = 2L/(3+sqrt 2)
+                        the support radius of the periodisation rule (Sec. 3.3)       */
+  double C_gamma;    /* VHS constant, B = C_gamma |q|^gamma; default 1                */
+  int radial_rank;   /* terms of the radial expansion of Btilde when gamma != 1;
+                        <= 0: 1 for gamma == 1 (exact decoupling), 16 otherwise       */
+  int inner_nodes;   /* Gauss-Legendre nodes of the inner radial integral, default 128 */
+  int project;       /* 1 (default): apply the conservation projection to Q          */
+} boltz_grid_opts;
+
+typedef struct boltz_grid_s* boltz_grid;
+
+/* A batch of cells that share one grid. */
+typedef struct {
+  boltz_grid grid;
+  int64_t n_cells;   /* number of cells, >= 0 (0 is a no-op)                          */
+  int prec;          /* a boltz_precision                                             */
+  int f_is_fp64;     /* 1: f and Q are float64; 0: float32                            */
+} boltz_batch;
+
+void boltz_default_opts(boltz_grid_opts* opts);
+
+/* Build a grid: velocity grid, direction set {e_j, w_j}, the separated kernel tables
+ * alpha_j(k) = Btilde phi(xi_k . e_j), alpha'_j(k) = psi(|Pi_{e_j-perp} xi_k|) on the
+ * full mode set (Sec. 3.3, 3D decoupling formula; psi is the disk transform
+ * 2 pi R J1(R s)/s), the loss multiplier D(k) = sum_j w_j alpha_j alpha'_j and the 5x5
+ * matrix of the projection (Sec. 3.2, Eq. minim1).  For gamma != 1 the kernel is not
+ * separable in 3D and a rank-r radial expansion is tabulated instead (r terms per
+ * direction).  Builds the tables on the host in float64 and copies them to the
+ * current device.
+ *   N_v     points per axis; supported: 16, 32.
+ *   L       half-width of the velocity box [-L, L)^3, > 0.
+ *   gamma   VHS exponent in [-3, 1] (1 = hard spheres, 0 = Maxwell molecules).
+ *   M_dirs  number of directions, 1..4096.
+ *   out     receives the handle; unchanged on error.
+ * Errors: EINVAL, EUNSUPPORTED (N_v), ENOMEM, ECUDA.  Blocking (host work + copies). */
+boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs,
+                               const boltz_grid_opts* opts, boltz_grid* out);
+
+/* Free the grid and its tables.  Synchronises the device first.  NULL is a no-op. */
+boltz_status boltz_destroy_grid(boltz_grid g);
+
+/* Q = Q(f, f) for every cell of the batch (Sec. 3.3), projected so that the moments
+ * of Q vanish (Sec. 3.2) unless the grid was built with project = 0.  f and Q are
+ * device arrays of n_cells * N^3 elements (float32 or float64 per f_is_fp64); they must
+ * not overlap.  One kernel launch on `stream`; HBM sees one read of f and one write of
+ * Q per cell.  Errors: EINVAL, EUNSUPPORTED (prec for this N), ECUDA. */
+boltz_status boltz_collide(const boltz_batch* b, const void* f, void* Q, void* stream);
+
+/* Advance the homogeneous relaxation df/dt = Q(f) (Sec. 3.1, Eq. relax) in place by
+ * `steps` steps of size dt.  rk_order 1: forward Euler f <- Pi(f + dt Q(f))
+ * (Eq. f_coll); rk_order 2: Heun, f1 = Pi(f + dt Q(f)), f <- Pi(f/2 + (f1 + dt Q(f1))/2).
+ * Pi projects onto the moments the cells had when the call started (Eq. minim1 with U
+ * fixed), so rounding does not accumulate in rho, rho u, E.  Uses library-owned scratch
+ * (one float64 moment row per cell, and one copy of f for rk_order 2), grown on demand
+ * and kept with the grid.  Errors: EINVAL (dt <= 0, steps < 0, rk_order), EUNSUPPORTED,
+ * ENOMEM, ECUDA. */
+boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, int rk_order,
+                         void* stream);
+
+/* U[c] = (rho, rho u, E) of every cell (Eq. i5 on the grid, Eq. DM), float64,
+ * U a device array of n_cells * 5 doubles.  Errors: EINVAL, ECUDA. */
+boltz_status boltz_moments(const boltz_batch* b, const void* f, double* U, void* stream);
+
+/* Synchronise `stream`, then read and clear the device status word of the current
+ * device.  Returns BOLTZ_OK, BOLTZ_ENONFINITE, or BOLTZ_ECUDA if the stream itself
+ * reported an error. */
+boltz_status boltz_stream_status(void* stream);
+
+/* Thread-local message of the last failing call of this thread ("" if none). */
+const char* boltz_last_error(void);
+
+/* Grid description for callers and tests.  Any output pointer may be NULL.
+ *   S, R       support radius and Carleman radius; M_eff = M_dirs * radial_rank. */
+boltz_status boltz_grid_info(boltz_grid g, int* N_v, double* L, double* dv, double* S,
+                             double* R, int* M_eff);
+
+/* Copy the float64 host tables out (for parity checks of the table builder):
+ * e [M_dirs * 3], w [M_eff], alpha [M_eff * N^3], alphap [M_eff * N^3], D [N^3], each in
+ * the (kx, ky, kz) FFT storage order of the mode numbers (index i holds k = i for
+ * i < N/2, else i - N).  Any pointer may be NULL; sizes are in elements. */
+boltz_status boltz_grid_tables(boltz_grid g, double* e, double* w, double* alpha,
+                               double* alphap, double* D);
+
+/* Version string of the library. */
+const char* boltz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOLTZ_H */

@@ -1,0 +1,214 @@
+"""Thin Python binding of libboltz (include/boltz.h), argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``libboltz.so``; this module converts
+torch tensors (or raw integers) into device pointers and status codes into
+exceptions.  There is no fallback: if the in-tree library is missing the first call
+raises ``BoltzError``.  Build it with ``python -m paper_1608_08009_gb300.build``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libboltz.so")
+
+BOLTZ_OK = 0
+BOLTZ_EINVAL = 1
+BOLTZ_ENOMEM = 2
+BOLTZ_ECUDA = 3
+BOLTZ_EUNSUPPORTED = 4
+BOLTZ_ENONFINITE = 5
+BOLTZ_ETIMEOUT = 6
+
+BOLTZ_FP64 = 0
+BOLTZ_FP32_FFT = 1
+BOLTZ_TF32_DFT = 2
+BOLTZ_3XBF16_DFT = 3
+BOLTZ_3XTF32_DFT = 4
+
+_STATUS_NAMES = {0: "BOLTZ_OK", 1: "BOLTZ_EINVAL", 2: "BOLTZ_ENOMEM", 3: "BOLTZ_ECUDA",
+                 4: "BOLTZ_EUNSUPPORTED", 5: "BOLTZ_ENONFINITE", 6: "BOLTZ_ETIMEOUT"}
+
+EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "boltz_collide",
+            "boltz_relax", "boltz_moments", "boltz_stream_status", "boltz_last_error",
+            "boltz_grid_info", "boltz_grid_tables", "boltz_version")
+
+
+class BoltzError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class boltz_grid_opts(ctypes.Structure):
+    _fields_ = [("dirs_kind", ctypes.c_int), ("dirs_a1", ctypes.c_int), ("R_trunc", ctypes.c_double),
+                ("C_gamma", ctypes.c_double), ("radial_rank", ctypes.c_int), ("inner_nodes", ctypes.c_int),
+                ("project", ctypes.c_int)]
+
+
+class boltz_batch(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("n_cells", ctypes.c_int64), ("prec", ctypes.c_int),
+                ("f_is_fp64", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree libboltz.so once (raises BoltzError if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise BoltzError(BOLTZ_ECUDA, f"libboltz.so not built ({LIB_PATH}); run the build first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        L.boltz_default_opts.argtypes = [P(boltz_grid_opts)]
+        L.boltz_default_opts.restype = None
+        L.boltz_create_grid.argtypes = [i32, f64, f64, i32, P(boltz_grid_opts), P(vp)]
+        L.boltz_destroy_grid.argtypes = [vp]
+        L.boltz_collide.argtypes = [P(boltz_batch), vp, vp, vp]
+        L.boltz_relax.argtypes = [P(boltz_batch), vp, f64, i32, i32, vp]
+        L.boltz_moments.argtypes = [P(boltz_batch), vp, vp, vp]
+        L.boltz_stream_status.argtypes = [vp]
+        L.boltz_last_error.argtypes = []
+        L.boltz_last_error.restype = ctypes.c_char_p
+        L.boltz_grid_info.argtypes = [vp, P(i32), P(f64), P(f64), P(f64), P(f64), P(i32)]
+        L.boltz_grid_tables.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.boltz_version.argtypes = []
+        L.boltz_version.restype = ctypes.c_char_p
+        for name in ("boltz_create_grid", "boltz_destroy_grid", "boltz_collide", "boltz_relax",
+                     "boltz_moments", "boltz_stream_status", "boltz_grid_info", "boltz_grid_tables"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != BOLTZ_OK:
+        raise BoltzError(status, lib().boltz_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    """Device (or host) address of a tensor / integer / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def boltz_default_opts() -> boltz_grid_opts:
+    o = boltz_grid_opts()
+    lib().boltz_default_opts(ctypes.byref(o))
+    return o
+
+
+def boltz_create_grid(N_v: int, L: float, gamma: float, M_dirs: int, opts: boltz_grid_opts | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().boltz_create_grid(N_v, L, gamma, M_dirs, ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def boltz_destroy_grid(grid: int) -> None:
+    _check(lib().boltz_destroy_grid(grid))
+
+
+def make_batch(grid: int, n_cells: int, prec: int, f_is_fp64: bool) -> boltz_batch:
+    return boltz_batch(grid, n_cells, prec, 1 if f_is_fp64 else 0)
+
+
+def boltz_collide(batch: boltz_batch, f, Q, stream=None) -> None:
+    _check(lib().boltz_collide(ctypes.byref(batch), _ptr(f), _ptr(Q), _stream(stream)))
+
+
+def boltz_relax(batch: boltz_batch, f, dt: float, steps: int, rk_order: int = 1, stream=None) -> None:
+    _check(lib().boltz_relax(ctypes.byref(batch), _ptr(f), dt, steps, rk_order, _stream(stream)))
+
+
+def boltz_moments(batch: boltz_batch, f, U, stream=None) -> None:
+    _check(lib().boltz_moments(ctypes.byref(batch), _ptr(f), _ptr(U), _stream(stream)))
+
+
+def boltz_stream_status(stream=None) -> None:
+    _check(lib().boltz_stream_status(_stream(stream)))
+
+
+def boltz_last_error() -> str:
+    return lib().boltz_last_error().decode()
+
+
+def boltz_version() -> str:
+    return lib().boltz_version().decode()
+
+
+def boltz_grid_info(grid: int) -> dict:
+    N = ctypes.c_int()
+    M = ctypes.c_int()
+    L, dv, S, R = (ctypes.c_double() for _ in range(4))
+    _check(lib().boltz_grid_info(grid, ctypes.byref(N), ctypes.byref(L), ctypes.byref(dv), ctypes.byref(S),
+                                 ctypes.byref(R), ctypes.byref(M)))
+    return {"N": N.value, "L": L.value, "dv": dv.value, "S": S.value, "R": R.value, "M_eff": M.value}
+
+
+def boltz_grid_tables(grid: int, M_dirs: int):
+    """Host float64 tables (e, w, alpha, alphap, D) as numpy arrays (for parity tests)."""
+    import numpy as np
+
+    info = boltz_grid_info(grid)
+    N, Me = info["N"], info["M_eff"]
+    n = N ** 3
+    e = np.empty(M_dirs * 3)
+    w = np.empty(Me)
+    al = np.empty(Me * n)
+    ap = np.empty(Me * n)
+    D = np.empty(n)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().boltz_grid_tables(grid, p(e), p(w), p(al), p(ap), p(D)))
+    return e.reshape(M_dirs, 3), w, al.reshape(Me, N, N, N), ap.reshape(Me, N, N, N), D.reshape(N, N, N)
+
+
+class Grid:
+    """Owning handle of a boltz grid (destroyed on close / garbage collection)."""
+
+    def __init__(self, N_v: int, L: float, gamma: float = 1.0, M_dirs: int = 64, **opts):
+        o = boltz_default_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.M_dirs = M_dirs
+        self.handle = boltz_create_grid(N_v, L, gamma, M_dirs, o)
+        self.info = boltz_grid_info(self.handle)
+
+    def batch(self, n_cells: int, prec: int = BOLTZ_FP64, f_is_fp64: bool = True) -> boltz_batch:
+        return make_batch(self.handle, n_cells, prec, f_is_fp64)
+
+    def tables(self):
+        return boltz_grid_tables(self.handle, self.M_dirs)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            boltz_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

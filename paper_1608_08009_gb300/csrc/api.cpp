@@ -1,0 +1,311 @@
+// C ABI of libboltz (declared in include/boltz.h): argument checking, grid ownership,
+// relaxation driver.  All compute happens in the kernels of collide.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace boltz {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+boltz_status read_and_clear_status(cudaStream_t stream, unsigned* value);
+
+}  // namespace boltz
+
+using boltz::set_error;
+
+static boltz_status check_batch(const boltz_batch* b) {
+  if (!b || !b->grid) {
+    set_error("null batch or grid");
+    return BOLTZ_EINVAL;
+  }
+  if (b->n_cells < 0) {
+    set_error("n_cells must be >= 0");
+    return BOLTZ_EINVAL;
+  }
+  if (b->n_cells > (int64_t)1 << 24) {
+    set_error("n_cells above 2^24 per call");
+    return BOLTZ_EINVAL;
+  }
+  if (b->f_is_fp64 != 0 && b->f_is_fp64 != 1) {
+    set_error("f_is_fp64 must be 0 or 1");
+    return BOLTZ_EINVAL;
+  }
+  if (b->prec < BOLTZ_FP64 || b->prec > BOLTZ_3XTF32_DFT) {
+    set_error("unknown precision");
+    return BOLTZ_EINVAL;
+  }
+  if (!boltz::collide_supported(b->grid->N, b->prec)) {
+    set_error("this precision has no kernel for this N in this build");
+    return BOLTZ_EUNSUPPORTED;
+  }
+  return BOLTZ_OK;
+}
+
+static boltz_status check_device(const boltz_grid_s* g) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return BOLTZ_ECUDA;
+  }
+  if (dev != g->device) {
+    set_error("the grid belongs to another device");
+    return BOLTZ_EINVAL;
+  }
+  return BOLTZ_OK;
+}
+
+extern "C" {
+
+void boltz_default_opts(boltz_grid_opts* o) {
+  if (!o) return;
+  o->dirs_kind = 0;
+  o->dirs_a1 = 0;
+  o->R_trunc = 0.0;
+  o->C_gamma = 1.0;
+  o->radial_rank = 0;
+  o->inner_nodes = 128;
+  o->project = 1;
+}
+
+boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, const boltz_grid_opts* opts,
+                               boltz_grid* out) {
+  if (!out) {
+    set_error("null output handle");
+    return BOLTZ_EINVAL;
+  }
+  if (N_v != 16 && N_v != 32) {
+    set_error("N_v must be 16 or 32 in this build");
+    return (N_v > 0 && N_v % 2 == 0) ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
+  }
+  if (!(L > 0) || !std::isfinite(L)) {
+    set_error("L must be positive and finite");
+    return BOLTZ_EINVAL;
+  }
+  if (!(gamma >= -3.0 && gamma <= 1.0)) {
+    set_error("gamma must lie in [-3, 1]");
+    return BOLTZ_EINVAL;
+  }
+  if (M_dirs < 1 || M_dirs > 4096) {
+    set_error("M_dirs must lie in [1, 4096]");
+    return BOLTZ_EINVAL;
+  }
+  boltz_grid_opts o;
+  boltz_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.C_gamma > 0) || !std::isfinite(o.C_gamma)) {
+    set_error("C_gamma must be positive");
+    return BOLTZ_EINVAL;
+  }
+  if (o.inner_nodes <= 0) o.inner_nodes = 128;
+  if (o.inner_nodes > 4096) {
+    set_error("inner_nodes must be <= 4096");
+    return BOLTZ_EINVAL;
+  }
+  int rank = o.radial_rank > 0 ? o.radial_rank : (gamma == 1.0 ? 1 : 16);
+  if (rank * (long long)M_dirs > 65536) {
+    set_error("M_dirs * radial_rank must be <= 65536");
+    return BOLTZ_EINVAL;
+  }
+  if (rank == 1 && gamma != 1.0) {
+    set_error("radial_rank 1 is exact only for gamma = 1");
+    return BOLTZ_EINVAL;
+  }
+  boltz_grid_s* g = new (std::nothrow) boltz_grid_s();
+  if (!g) {
+    set_error("out of host memory");
+    return BOLTZ_ENOMEM;
+  }
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return BOLTZ_ECUDA;
+  }
+  g->N = N_v;
+  g->L = L;
+  g->gamma = gamma;
+  g->C_gamma = o.C_gamma;
+  g->M = M_dirs;
+  g->rank = rank;
+  g->dirs_kind = o.dirs_kind;
+  g->a1 = o.dirs_a1;
+  g->inner_nodes = o.inner_nodes;
+  g->project = o.project ? 1 : 0;
+  g->R = o.R_trunc > 0 ? o.R_trunc : 0.0;
+  boltz_status st = boltz::build_tables(g);
+  if (st == BOLTZ_OK) st = boltz::upload_tables(g);
+  if (st != BOLTZ_OK) {
+    boltz_destroy_grid(g);
+    return st;
+  }
+  *out = g;
+  return BOLTZ_OK;
+}
+
+boltz_status boltz_destroy_grid(boltz_grid g) {
+  if (!g) return BOLTZ_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  cudaFree(g->tab64);
+  cudaFree(g->tab32);
+  cudaFree(g->w_dev);
+  cudaFree(g->U0);
+  cudaFree(g->stage);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete g;
+  return BOLTZ_OK;
+}
+
+boltz_status boltz_collide(const boltz_batch* b, const void* f, void* Q, void* stream) {
+  boltz_status st = check_batch(b);
+  if (st != BOLTZ_OK) return st;
+  if (b->n_cells == 0) return BOLTZ_OK;
+  if (!f || !Q) {
+    set_error("null f or Q");
+    return BOLTZ_EINVAL;
+  }
+  if (f == Q) {
+    set_error("f and Q must not overlap");
+    return BOLTZ_EINVAL;
+  }
+  if ((st = check_device(b->grid)) != BOLTZ_OK) return st;
+  return boltz::launch_collide(b->grid, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, Q, 0.0, 0.0, 1.0, nullptr,
+                               b->grid->project, (cudaStream_t)stream);
+}
+
+boltz_status boltz_moments(const boltz_batch* b, const void* f, double* U, void* stream) {
+  if (!b || !b->grid || b->n_cells < 0 || (b->f_is_fp64 != 0 && b->f_is_fp64 != 1)) {
+    set_error("bad batch");
+    return BOLTZ_EINVAL;
+  }
+  if (b->n_cells == 0) return BOLTZ_OK;
+  if (!f || !U) {
+    set_error("null f or U");
+    return BOLTZ_EINVAL;
+  }
+  boltz_status st = check_device(b->grid);
+  if (st != BOLTZ_OK) return st;
+  const double dv3 = b->grid->dv * b->grid->dv * b->grid->dv;
+  return boltz::launch_phisums(b->grid, b->n_cells, b->f_is_fp64, f, U, dv3, (cudaStream_t)stream);
+}
+
+boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, int rk_order, void* stream) {
+  boltz_status st = check_batch(b);
+  if (st != BOLTZ_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) {
+    set_error("dt must be positive and finite");
+    return BOLTZ_EINVAL;
+  }
+  if (steps < 0) {
+    set_error("steps must be >= 0");
+    return BOLTZ_EINVAL;
+  }
+  if (rk_order != 1 && rk_order != 2) {
+    set_error("rk_order must be 1 or 2");
+    return BOLTZ_EINVAL;
+  }
+  if (b->n_cells == 0 || steps == 0) return BOLTZ_OK;
+  if (!f) {
+    set_error("null f");
+    return BOLTZ_EINVAL;
+  }
+  if ((st = check_device(b->grid)) != BOLTZ_OK) return st;
+  boltz_grid_s* g = b->grid;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t esz = b->f_is_fp64 ? 8 : 4;
+  // scratch: moment targets (and the Heun stage), grown on demand, owned by the grid
+  if ((size_t)b->n_cells > g->U0_cap) {
+    cudaStreamSynchronize(s);
+    cudaFree(g->U0);
+    g->U0 = nullptr;
+    g->U0_cap = 0;
+    if (cudaMalloc(&g->U0, (size_t)b->n_cells * 5 * sizeof(double)) != cudaSuccess) {
+      set_error("relax scratch allocation failed");
+      return BOLTZ_ENOMEM;
+    }
+    g->U0_cap = (size_t)b->n_cells;
+  }
+  const size_t stage_bytes = (size_t)b->n_cells * n * esz;
+  if (rk_order == 2 && stage_bytes > g->stage_cap) {
+    cudaStreamSynchronize(s);
+    cudaFree(g->stage);
+    g->stage = nullptr;
+    g->stage_cap = 0;
+    if (cudaMalloc(&g->stage, stage_bytes) != cudaSuccess) {
+      set_error("relax scratch allocation failed");
+      return BOLTZ_ENOMEM;
+    }
+    g->stage_cap = stage_bytes;
+  }
+  // targets: Phi-sums of the initial state (Eq. minim1 with U fixed)
+  st = boltz::launch_phisums(g, b->n_cells, b->f_is_fp64, f, g->U0, 1.0, s);
+  if (st != BOLTZ_OK) return st;
+  for (int it = 0; it < steps; ++it) {
+    if (rk_order == 1) {
+      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, g->U0, 1, s);
+      if (st != BOLTZ_OK) return st;
+    } else {
+      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, g->stage, 0.0, 1.0, dt, g->U0,
+                                 1, s);
+      if (st != BOLTZ_OK) return st;
+      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, g->stage, f, f, 0.5, 0.5, 0.5 * dt, g->U0,
+                                 1, s);
+      if (st != BOLTZ_OK) return st;
+    }
+  }
+  return BOLTZ_OK;
+}
+
+boltz_status boltz_stream_status(void* stream) {
+  unsigned v = 0;
+  boltz_status st = boltz::read_and_clear_status((cudaStream_t)stream, &v);
+  if (st != BOLTZ_OK) return st;
+  if (v & 1u) {
+    set_error("a non-finite value was produced on the device");
+    return BOLTZ_ENONFINITE;
+  }
+  return BOLTZ_OK;
+}
+
+const char* boltz_last_error(void) { return boltz::t_last_error.c_str(); }
+
+boltz_status boltz_grid_info(boltz_grid g, int* N_v, double* L, double* dv, double* S, double* R, int* M_eff) {
+  if (!g) {
+    set_error("null grid");
+    return BOLTZ_EINVAL;
+  }
+  if (N_v) *N_v = g->N;
+  if (L) *L = g->L;
+  if (dv) *dv = g->dv;
+  if (S) *S = g->S;
+  if (R) *R = g->R;
+  if (M_eff) *M_eff = g->M_eff;
+  return BOLTZ_OK;
+}
+
+boltz_status boltz_grid_tables(boltz_grid g, double* e, double* w, double* alpha, double* alphap, double* D) {
+  if (!g) {
+    set_error("null grid");
+    return BOLTZ_EINVAL;
+  }
+  if (e) std::memcpy(e, g->e.data(), g->e.size() * sizeof(double));
+  if (w) std::memcpy(w, g->w.data(), g->w.size() * sizeof(double));
+  if (alpha) std::memcpy(alpha, g->alpha.data(), g->alpha.size() * sizeof(double));
+  if (alphap) std::memcpy(alphap, g->alphap.data(), g->alphap.size() * sizeof(double));
+  if (D) std::memcpy(D, g->D.data(), g->D.size() * sizeof(double));
+  return BOLTZ_OK;
+}
+
+const char* boltz_version(void) { return "libboltz 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,483 @@
+// Fused per-cell kernels of the fast spectral collision operator (sm_103a).
+//
+// Paper: arxiv 1608.08009.  Per cell (Sec. 4.2): one forward 3D transform of f
+// (Eq. FC), then for every separated quadrature term j the coefficients
+// (alpha_j + i alpha'_j) fhat and one inverse 3D transform (Eq. FU) whose real and
+// imaginary parts are the two factors of the gain term (Sec. 3.3, decoupling formula),
+// accumulated as Q+ += w_j Re Im; then the loss term L = inverse(D fhat), Q = Q+ - f L,
+// the conservation projection (Sec. 3.2, Eq. minim1) and optionally the collision step
+// f <- f + dt Q (Eq. f_coll), all in one launch: f is read once and Q (or the new f)
+// written once per cell.
+//
+// Work decomposition.  A cell is owned by a thread-block cluster of C CTAs.
+//  * Spectrum: CTA c keeps fhat(kx, ky, kz) for the ky-slab [c N/C, (c+1) N/C) in shared
+//    memory, all kx and kz.
+//  * Physical space: CTA q owns the x-slab [q N/C, (q+1) N/C); the gain accumulator of
+//    its points lives in registers (thread (x, z) holds the N values along y).
+//  * One inverse 3D transform = pass along kx (pencils of the CTA's ky-slab, in
+//    registers) whose N outputs are scattered by x into the owners' shared memory through
+//    distributed shared memory, a cluster barrier, then the passes along kz and ky inside
+//    each x-plane of the owner.
+//  * Every 1D pass is a fully unrolled radix-2 FFT of one pencil held by one thread.
+// Twiddles, kernel tables and weights are float32 for the BOLTZ_FP32_FFT path and
+// float64 for BOLTZ_FP64.  Moments, projection and the update are float64 in both.
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "fft_regs.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace boltz {
+
+// Device status word of this device: bit 0 = a non-finite value was written.
+__device__ unsigned int g_boltz_status;
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T> __device__ __forceinline__ typename Vec2<T>::type mk2(T a, T b);
+template <> __device__ __forceinline__ float2 mk2<float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ double2 mk2<double>(double a, double b) { return make_double2(a, b); }
+
+struct CollideArgs {
+  const void* f_in;    // [cells][N^3] TIO
+  const void* f_base;  // [cells][N^3] TIO or null
+  void* out;           // [cells][N^3] TIO
+  const void* tab;     // [(M_eff + 1) * N^3] (alpha, alpha') as Vec2<T>; last entry (D, 0)
+  const double* w;     // [M_eff]
+  const double* Utgt;  // [cells][5] target Phi-sums, or null (target 0)
+  double a, b, s;      // out = Pi(a f_base + b f_in + s Q)
+  int M_eff;
+  int project;
+  KernelGeom geom;
+};
+
+template <typename T, int N, int C>
+struct CollideCfg {
+  static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
+  static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
+  static constexpr int ROW = N + 1;         // padded row of the x-plane buffer
+  static constexpr int WARPS = THREADS / 32;
+  using T2 = typename Vec2<T>::type;
+  static constexpr size_t FH = (size_t)N * NP * N;   // spectrum slab [kx][kyl][kz]
+  static constexpr size_t XB = (size_t)NP * N * ROW; // x-plane buffer [xl][ky][kz|z]
+  static constexpr size_t SMEM = (FH + XB) * sizeof(T2) + (size_t)(WARPS + 1) * 5 * sizeof(double);
+  static_assert(THREADS % 32 == 0, "whole warps");
+};
+
+template <int C>
+__device__ __forceinline__ void cluster_barrier() {
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+template <int C, typename P>
+__device__ __forceinline__ P* cta_smem(P* p, int r) {
+  if constexpr (C > 1) {
+    return cg::this_cluster().map_shared_rank(p, (unsigned)r);
+  } else {
+    return p;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, typename TIO, int N, int C>
+__global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, 1)
+collide_kernel(const CollideArgs args) {
+  using Cfg = CollideCfg<T, N, C>;
+  using T2 = typename Cfg::T2;
+  constexpr int NP = Cfg::NP, ROW = Cfg::ROW, WARPS = Cfg::WARPS;
+  constexpr int n = N * N * N;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* Fh = reinterpret_cast<T2*>(smem_raw);
+  T2* XB = Fh + Cfg::FH;
+  double* red = reinterpret_cast<double*>(XB + Cfg::XB);
+
+  const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  const long long cell = blockIdx.x / C;
+  const int t = threadIdx.x;
+  const int tA = t / N, tB = t % N;
+  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+
+  T re[N], im[N];
+
+  // ---- forward transform, pass along y: thread (x = rank NP + tA, z = tB) ----------
+  {
+    const int x = rank * NP + tA;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      re[y] = (T)fin[(x * N + y) * N + tB];
+      im[y] = T(0);
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) XB[(tA * N + k) * ROW + tB] = mk2<T>(re[k], im[k]);
+  }
+  __syncthreads();
+  // ---- pass along z: thread (xl = tA, ky = tB) ---------------------------------------
+  {
+    T2* row = XB + (tA * N + tB) * ROW;
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const T2 v = row[z];
+      re[z] = v.x;
+      im[z] = v.y;
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) row[k] = mk2<T>(re[k], im[k]);
+  }
+  cluster_barrier<C>();
+  // ---- pass along x (remote x-planes): thread (kyl = tA, kz = tB) --------------------
+  {
+    const int ky = rank * NP + tA;
+#pragma unroll
+    for (int x = 0; x < N; ++x) {
+      const T2 v = cta_smem<C>(XB, x / NP)[((x % NP) * N + ky) * ROW + tB];
+      re[x] = v.x;
+      im[x] = v.y;
+    }
+    fft_regs<N, -1>(re, im);
+    const T scale = T(1) / T(n);
+    const bool nyq = (ky == N / 2) || (tB == N / 2);
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      // Every mode with a component -N/2 is removed so each inverse transform is real.
+      const bool z0 = nyq || (kx == N / 2);
+      Fh[(kx * NP + tA) * N + tB] = z0 ? mk2<T>(T(0), T(0)) : mk2<T>(re[kx] * scale, im[kx] * scale);
+    }
+  }
+  cluster_barrier<C>();
+
+  // ---- angular loop: one complex inverse transform per separated term --------------
+  T acc[N];
+#pragma unroll
+  for (int y = 0; y < N; ++y) acc[y] = T(0);
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  for (int j = 0; j <= M_eff; ++j) {
+    {  // pass along kx with the coefficients: thread (kyl = tA, kz = tB)
+      const int ky = rank * NP + tA;
+      const T2* tj = tab + (size_t)j * n + ky * N + tB;
+#pragma unroll
+      for (int kx = 0; kx < N; ++kx) {
+        const T2 c = Fh[(kx * NP + tA) * N + tB];
+        const T2 ab = __ldg(tj + kx * N * N);
+        re[kx] = ab.x * c.x - ab.y * c.y;
+        im[kx] = ab.x * c.y + ab.y * c.x;
+      }
+      fft_regs<N, +1>(re, im);
+#pragma unroll
+      for (int x = 0; x < N; ++x) cta_smem<C>(XB, x / NP)[((x % NP) * N + ky) * ROW + tB] = mk2<T>(re[x], im[x]);
+    }
+    cluster_barrier<C>();
+    {  // pass along kz: thread (xl = tA, ky = tB)
+      T2* row = XB + (tA * N + tB) * ROW;
+#pragma unroll
+      for (int z = 0; z < N; ++z) {
+        const T2 v = row[z];
+        re[z] = v.x;
+        im[z] = v.y;
+      }
+      fft_regs<N, +1>(re, im);
+#pragma unroll
+      for (int z = 0; z < N; ++z) row[z] = mk2<T>(re[z], im[z]);
+    }
+    __syncthreads();
+    {  // pass along ky: thread (xl = tA, z = tB); outputs along y
+#pragma unroll
+      for (int ky = 0; ky < N; ++ky) {
+        const T2 v = XB[(tA * N + ky) * ROW + tB];
+        re[ky] = v.x;
+        im[ky] = v.y;
+      }
+      fft_regs<N, +1>(re, im);
+      if (j < M_eff) {
+        const T wj = (T)args.w[j];
+#pragma unroll
+        for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
+      }
+      // for j == M_eff, re[] now holds the loss multiplier L(v) along y
+    }
+    if (j < M_eff) cluster_barrier<C>();
+  }
+
+  // ---- Q = Q+ - f L, projection and update (float64) ---------------------------------
+  const int x = rank * NP + tA;
+  const double L = args.geom.L, dv = args.geom.dv;
+  const double vx = -L + x * dv, vz = -L + tB * dv;
+  const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
+  double g[N];
+  double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const int idx = (x * N + y) * N + tB;
+    const TIO fv = fin[idx];
+    const T q = acc[y] - (T)fv * re[y];
+    double gv = args.s * (double)q;
+    if (args.b != 0.0) gv += args.b * (double)fv;
+    if (fb) gv += args.a * (double)fb[idx];
+    g[y] = gv;
+    const double vy = -L + y * dv;
+    m[0] += gv;
+    m[1] += gv * vx;
+    m[2] += gv * vy;
+    m[3] += gv * vz;
+    m[4] += gv * (0.5 * (vx * vx + vy * vy + vz * vz));
+  }
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const double s = warp_sum(m[r]);
+    if (lane == 0) red[warp * 5 + r] = s;
+  }
+  __syncthreads();
+  if (t < 5) {
+    double s = 0.0;
+    for (int w = 0; w < WARPS; ++w) s += red[w * 5 + t];
+    red[WARPS * 5 + t] = s;  // this CTA's partial sums
+  }
+  cluster_barrier<C>();
+  double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (args.project) {
+    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < C; ++q) {
+      const double* p = cta_smem<C>(red + WARPS * 5, q);
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tot[r] += p[r];
+    }
+    double rhs[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) rhs[r] = (args.Utgt ? args.Utgt[cell * 5 + r] : 0.0) - tot[r];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += args.geom.G[r * 5 + k] * rhs[k];
+      c5[r] = s;
+    }
+  }
+  cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
+  TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
+  bool bad = false;
+  const double base = c5[0] + c5[1] * vx + c5[3] * vz;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double vy = -L + y * dv;
+    const double val = g[y] + base + c5[2] * vy + c5[4] * (0.5 * (vx * vx + vy * vy + vz * vz));
+    bad |= !isfinite(val);
+    out[(x * N + y) * N + tB] = (TIO)val;
+  }
+  if (bad) atomicOr(&g_boltz_status, 1u);
+}
+
+// Plain sums Phi f per cell, scaled: U[c][r] = scale * sum_v phi_r(v) f(v).
+template <typename TIO>
+__global__ void __launch_bounds__(256) phisums_kernel(const TIO* f, double* U, int N, double L, double dv,
+                                                      double scale) {
+  const long long cell = blockIdx.x;
+  const int n = N * N * N;
+  const TIO* fc = f + cell * n;
+  double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int x = idx / (N * N), y = (idx / N) % N, z = idx % N;
+    const double vx = -L + x * dv, vy = -L + y * dv, vz = -L + z * dv;
+    const double fv = (double)fc[idx];
+    m[0] += fv;
+    m[1] += fv * vx;
+    m[2] += fv * vy;
+    m[3] += fv * vz;
+    m[4] += fv * (0.5 * (vx * vx + vy * vy + vz * vz));
+  }
+  __shared__ double red[8][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const double s = warp_sum(m[r]);
+    if (lane == 0) red[warp][r] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    U[cell * 5 + threadIdx.x] = scale * s;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+
+static boltz_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return BOLTZ_ECUDA;
+}
+
+boltz_status upload_tables(boltz_grid_s* g) {
+  // twiddles exp(2 pi i m / 64), host libm in float64
+  double tc[64], ts[64];
+  float fc[64], fs[64];
+  for (int m = 0; m < 64; ++m) {
+    const double ang = 2.0 * 3.14159265358979323846 * m / 64.0;
+    tc[m] = std::cos(ang);
+    ts[m] = std::sin(ang);
+    fc[m] = (float)tc[m];
+    fs[m] = (float)ts[m];
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_twc64, tc, sizeof(tc))) != cudaSuccess) return cuda_fail(e, "twiddle upload");
+  if ((e = cudaMemcpyToSymbol(c_tws64, ts, sizeof(ts))) != cudaSuccess) return cuda_fail(e, "twiddle upload");
+  if ((e = cudaMemcpyToSymbol(c_twc32, fc, sizeof(fc))) != cudaSuccess) return cuda_fail(e, "twiddle upload");
+  if ((e = cudaMemcpyToSymbol(c_tws32, fs, sizeof(fs))) != cudaSuccess) return cuda_fail(e, "twiddle upload");
+
+  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t entries = (size_t)(g->M_eff + 1) * n;
+  std::vector<double2> h64;
+  std::vector<float2> h32;
+  try {
+    h64.resize(entries);
+    h32.resize(entries);
+  } catch (...) {
+    set_error("host staging of the device tables failed");
+    return BOLTZ_ENOMEM;
+  }
+  for (int i = 0; i < g->M_eff; ++i)
+    for (size_t k = 0; k < n; ++k) {
+      const double a = g->alpha[(size_t)i * n + k], b = g->alphap[(size_t)i * n + k];
+      h64[(size_t)i * n + k] = make_double2(a, b);
+      h32[(size_t)i * n + k] = make_float2((float)a, (float)b);
+    }
+  for (size_t k = 0; k < n; ++k) {
+    h64[(size_t)g->M_eff * n + k] = make_double2(g->D[k], 0.0);
+    h32[(size_t)g->M_eff * n + k] = make_float2((float)g->D[k], 0.0f);
+  }
+  if ((e = cudaMalloc(&g->tab64, entries * sizeof(double2))) != cudaSuccess) {
+    set_error(std::string("device tables: ") + cudaGetErrorString(e));
+    return BOLTZ_ENOMEM;
+  }
+  if ((e = cudaMalloc(&g->tab32, entries * sizeof(float2))) != cudaSuccess) {
+    set_error(std::string("device tables: ") + cudaGetErrorString(e));
+    return BOLTZ_ENOMEM;
+  }
+  if ((e = cudaMalloc(&g->w_dev, (size_t)std::max(1, g->M_eff) * sizeof(double))) != cudaSuccess) {
+    set_error(std::string("device tables: ") + cudaGetErrorString(e));
+    return BOLTZ_ENOMEM;
+  }
+  if ((e = cudaMemcpy(g->tab64, h64.data(), entries * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "table upload");
+  if ((e = cudaMemcpy(g->tab32, h32.data(), entries * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "table upload");
+  if ((e = cudaMemcpy(g->w_dev, g->w.data(), g->M_eff * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "table upload");
+  return BOLTZ_OK;
+}
+
+template <typename T, typename TIO, int N, int C>
+static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  using Cfg = CollideCfg<T, N, C>;
+  auto kern = collide_kernel<T, TIO, N, C>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  if (C > 1) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_cells * C), 1, 1);
+  cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (C > 1) ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return cuda_fail(e, "collide launch");
+  return BOLTZ_OK;
+}
+
+bool collide_supported(int N, int prec) {
+  return (N == 16 || N == 32) && (prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT);
+}
+
+template <typename T, typename TIO>
+static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  constexpr bool dbl = sizeof(T) == 8;
+  if (g->N == 16) return launch_impl<T, TIO, 16, dbl ? 2 : 1>(a, n_cells, st);
+  if (g->N == 32) return launch_impl<T, TIO, 32, dbl ? 8 : 4>(a, n_cells, st);
+  set_error("no collision kernel for this N");
+  return BOLTZ_EUNSUPPORTED;
+}
+
+boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, const void* f_in,
+                            const void* f_base, void* out, double a, double b, double s, const double* Utgt,
+                            int project, cudaStream_t stream) {
+  if (n_cells == 0) return BOLTZ_OK;
+  if (!collide_supported(g->N, prec)) {
+    set_error("unsupported (N, precision) combination");
+    return BOLTZ_EUNSUPPORTED;
+  }
+  CollideArgs args;
+  args.f_in = f_in;
+  args.f_base = f_base;
+  args.out = out;
+  args.w = g->w_dev;
+  args.Utgt = Utgt;
+  args.a = a;
+  args.b = b;
+  args.s = s;
+  args.M_eff = g->M_eff;
+  args.project = project;
+  args.geom.L = g->L;
+  args.geom.dv = g->dv;
+  for (int i = 0; i < 25; ++i) args.geom.G[i] = g->proj.G[i];
+  if (prec == BOLTZ_FP64) {
+    args.tab = g->tab64;
+    return f_is_fp64 ? dispatch_n<double, double>(g, args, n_cells, stream)
+                     : dispatch_n<double, float>(g, args, n_cells, stream);
+  }
+  args.tab = g->tab32;
+  return f_is_fp64 ? dispatch_n<float, double>(g, args, n_cells, stream)
+                   : dispatch_n<float, float>(g, args, n_cells, stream);
+}
+
+boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f, double* U,
+                            double scale, cudaStream_t stream) {
+  if (n_cells == 0) return BOLTZ_OK;
+  dim3 grid((unsigned)n_cells), block(256);
+  if (f_is_fp64)
+    phisums_kernel<double><<<grid, block, 0, stream>>>((const double*)f, U, g->N, g->L, g->dv, scale);
+  else
+    phisums_kernel<float><<<grid, block, 0, stream>>>((const float*)f, U, g->N, g->L, g->dv, scale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+  return BOLTZ_OK;
+}
+
+boltz_status read_and_clear_status(cudaStream_t stream, unsigned* value) {
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  unsigned v = 0, zero = 0;
+  if ((e = cudaMemcpyFromSymbol(&v, g_boltz_status, sizeof(v))) != cudaSuccess) return cuda_fail(e, "status read");
+  if ((e = cudaMemcpyToSymbol(g_boltz_status, &zero, sizeof(zero))) != cudaSuccess) return cuda_fail(e, "status clear");
+  *value = v;
+  return BOLTZ_OK;
+}
+
+}  // namespace boltz

@@ -1,0 +1,65 @@
+// Internal declarations shared by the host table builder and the CUDA kernels of libboltz.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/boltz.h"
+
+namespace boltz {
+
+// Projection data of one grid (Sec. 3.2, Eq. minim1): with Phi the 5 x n matrix of the
+// rows (1, v_x, v_y, v_z, |v|^2/2) at the grid points, C = dv^3 Phi and
+// C^T (C C^T)^-1 (U - C g) = Phi^T G (U / dv^3 - Phi g), G = (Phi Phi^T)^-1.
+struct Projection {
+  double G[25];
+};
+
+// Geometry and kernel parameters passed by value to every collision kernel.
+struct KernelGeom {
+  double L;
+  double dv;
+  double G[25];
+};
+
+}  // namespace boltz
+
+struct boltz_grid_s {
+  int N = 0;
+  double L = 0, dv = 0, S = 0, R = 0, gamma = 1, C_gamma = 1;
+  int M = 0, rank = 1, M_eff = 0;
+  int dirs_kind = 0, a1 = 0, inner_nodes = 128, project = 1;
+  int device = 0;
+  // float64 host tables, mode storage order (kx, ky, kz), kz fastest
+  std::vector<double> e, wdir, w, alpha, alphap, D;
+  boltz::Projection proj{};
+  // device tables: (M_eff + 1) * n pairs (alpha, alpha'); entry M_eff holds (D, 0)
+  double2* tab64 = nullptr;
+  float2* tab32 = nullptr;
+  double* w_dev = nullptr;  // [M_eff]
+  // scratch of boltz_relax, grown on demand
+  double* U0 = nullptr;
+  size_t U0_cap = 0;  // cells
+  void* stage = nullptr;
+  size_t stage_cap = 0;  // bytes
+};
+
+namespace boltz {
+
+void set_error(const std::string& msg);
+
+// Host table builder (tables.cpp): fills e, wdir, w, alpha, alphap, D, proj, S, R.
+boltz_status build_tables(boltz_grid_s* g);
+
+// Kernel launchers (collide.cu).
+boltz_status upload_tables(boltz_grid_s* g);
+boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64,
+                            const void* f_in, const void* f_base, void* out, double a, double b,
+                            double s, const double* Utgt, int project, cudaStream_t stream);
+boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
+                            double* U, double scale, cudaStream_t stream);
+bool collide_supported(int N, int prec);
+
+}  // namespace boltz

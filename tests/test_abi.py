@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every entry point include/boltz.h declares.
+
+CPU only: no compute call is made; argument errors are checked before any CUDA call.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1608_08009_gb300 import boltz as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libboltz():
+    if not os.path.exists(B.LIB_PATH):
+        from paper_1608_08009_gb300 import build
+        build.build()
+    return B.lib()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(boltz_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(libboltz):
+    decl = declared_functions()
+    assert "boltz_collide" in decl and "boltz_relax" in decl and "boltz_moments" in decl
+    for name in decl:
+        assert hasattr(libboltz, name), name
+    assert set(B.EXPORTED) <= set(decl)
+
+
+def test_version_string(libboltz):
+    assert "sm_103a" in B.boltz_version()
+
+
+def test_default_opts(libboltz):
+    o = B.boltz_default_opts()
+    assert o.dirs_kind == 0 and o.project == 1 and o.C_gamma == 1.0 and o.inner_nodes == 128
+
+
+def test_argument_errors_without_device(libboltz):
+    L = libboltz
+    assert L.boltz_collide(None, None, None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_relax(None, None, 0.1, 1, 1, None) == B.BOLTZ_EINVAL
+    assert L.boltz_moments(None, None, None, None) == B.BOLTZ_EINVAL
+    h = ctypes.c_void_p()
+    assert L.boltz_create_grid(15, 8.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert L.boltz_create_grid(64, 8.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EUNSUPPORTED
+    assert L.boltz_create_grid(32, -1.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert L.boltz_create_grid(32, 8.0, 2.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert L.boltz_create_grid(32, 8.0, 1.0, 0, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert L.boltz_create_grid(32, 8.0, 1.0, 64, None, None) == B.BOLTZ_EINVAL
+    assert h.value is None
+    assert "L must be" in B.boltz_last_error() or len(B.boltz_last_error()) > 0
+    assert L.boltz_destroy_grid(None) == B.BOLTZ_OK
+    assert L.boltz_grid_info(None, None, None, None, None, None, None) == B.BOLTZ_EINVAL

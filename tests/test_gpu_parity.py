@@ -1,0 +1,229 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over all cells and velocities, ||Q_gpu - Q_ref|| / ||Q_ref||):
+  * BOLTZ_FP64      <= 1e-12
+  * BOLTZ_FP32_FFT  <= 1.25 * eps32 * log2(n) * kappa, eps32 = 2^-24, n = N^3 and
+    kappa = ||Q+|| / ||Q|| of the input (from the oracle): a float32 radix-2 transform
+    of n points has a relative L2 error of about eps32 log2(n); the gain Q+ and the
+    loss f L are each computed with that relative error and Q = Q+ - f L is kappa
+    times smaller than either.  (The moments, projection and update are float64.)
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1608_08009_gb300 import boltz as B
+from paper_1608_08009_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+def fp32_tol(f, og):
+    Qp, Lo = O.operator.gain_loss(f, og)
+    kappa = np.linalg.norm(Qp) / np.linalg.norm(Qp - f * Lo)
+    return 1.25 * EPS32 * math.log2(og.n) * kappa
+
+
+def tol_for(prec, f, og):
+    return 1e-12 if prec == B.BOLTZ_FP64 else fp32_tol(f, og)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+    yield
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+_oracle_grids = {}
+
+
+def oracle_grid(N, L, M, kind=0, gamma=1.0, **kw):
+    key = (N, L, M, kind, gamma, tuple(sorted(kw.items())))
+    if key not in _oracle_grids:
+        _oracle_grids[key] = O.make_grid(N, L, gamma=gamma, M=M, dirs_kind=kind, **kw)
+    return _oracle_grids[key]
+
+
+def run_collide(grid, f_np, prec, fp64=True, stream=None):
+    dt = torch.float64 if fp64 else torch.float32
+    f = torch.from_numpy(f_np).to(device="cuda", dtype=dt)
+    Q = torch.empty_like(f)
+    B.boltz_collide(grid.batch(f.shape[0], prec, fp64), f, Q, stream)
+    B.boltz_stream_status(stream)
+    return Q.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("N,L,M,kind", [(16, 6.0, 32, 0), (32, 8.0, 64, 0), (32, 8.0, 36, 2), (16, 5.0, 20, 1)])
+def test_tables_match_oracle(N, L, M, kind):
+    with B.Grid(N, L, 1.0, M, dirs_kind=kind) as g:
+        e, w, al, ap, D = g.tables()
+    og = oracle_grid(N, L, M, kind)
+    assert np.max(np.abs(e - og.e)) < 1e-15
+    assert np.max(np.abs(w - og.w)) < 1e-15
+    assert np.max(np.abs(al - og.alpha)) < 1e-13 * np.abs(og.alpha).max()
+    assert np.max(np.abs(ap - og.alphap)) < 1e-13 * np.abs(og.alphap).max()
+    assert np.max(np.abs(D - og.D)) < 1e-13 * np.abs(og.D).max()
+
+
+@pytest.mark.parametrize("prec", [B.BOLTZ_FP64, B.BOLTZ_FP32_FFT])
+@pytest.mark.parametrize("N,L,M,cells", [(16, 6.0, 32, 5), (32, 8.0, 64, 3)])
+def test_collide_parity(prec, N, L, M, cells):
+    f = W.two_maxwellians(cells, N, L, seed=20161 + N)
+    og = oracle_grid(N, L, M)
+    Qref = O.collide(f, og)
+    with B.Grid(N, L, 1.0, M) as g:
+        Q = run_collide(g, f, prec, fp64=True)
+    err = rel_l2(Q, Qref)
+    assert err <= tol_for(prec, f, og), err
+
+
+def test_collide_fp32_storage():
+    """f stored as float32: compare with the oracle on the same rounded input."""
+    N, L, M = 32, 8.0, 64
+    f = W.two_maxwellians(2, N, L, seed=7).astype(np.float32)
+    og = oracle_grid(N, L, M)
+    Qref = O.collide(f.astype(np.float64), og)
+    with B.Grid(N, L, 1.0, M) as g:
+        Q32 = run_collide(g, f, B.BOLTZ_FP32_FFT, fp64=False)
+        Q64 = run_collide(g, f.astype(np.float64), B.BOLTZ_FP64, fp64=False)
+    assert rel_l2(Q32, Qref) <= fp32_tol(f.astype(np.float64), og)
+    # float64 arithmetic on float32 storage: only the output rounding remains
+    assert rel_l2(Q64, Qref) <= 1e-7
+
+
+def test_collide_unprojected_and_other_directions():
+    N, L, M = 16, 5.0, 24
+    f = W.two_maxwellians(3, N, L, seed=99)
+    og = oracle_grid(N, L, M, kind=2)
+    Qref = O.collide(f, og, project=False)
+    with B.Grid(N, L, 1.0, M, dirs_kind=2, project=0) as g:
+        Q = run_collide(g, f, B.BOLTZ_FP64)
+    assert rel_l2(Q, Qref) <= 1e-12
+
+
+def test_gamma_rank_expansion():
+    """gamma = 0 (Maxwell molecules) through the rank-r radial expansion."""
+    N, L, M = 16, 6.0, 16
+    f = W.two_maxwellians(2, N, L, seed=5)
+    og = oracle_grid(N, L, M, kind=2, gamma=0.0, C_gamma=1 / (4 * math.pi), rank=6, inner_nodes=64)
+    Qref = O.collide(f, og)
+    with B.Grid(N, L, 0.0, M, dirs_kind=2, C_gamma=1 / (4 * math.pi), radial_rank=6, inner_nodes=64) as g:
+        assert g.info["M_eff"] == M * 6
+        Q = run_collide(g, f, B.BOLTZ_FP64)
+    assert rel_l2(Q, Qref) <= 1e-11
+
+
+def test_moments_parity():
+    N, L = 32, 8.0
+    f = W.two_maxwellians(4, N, L, seed=3)
+    with B.Grid(N, L, 1.0, 8) as g:
+        ft = torch.from_numpy(f).cuda()
+        U = torch.empty(4, 5, dtype=torch.float64, device="cuda")
+        B.boltz_moments(g.batch(4), ft, U)
+        B.boltz_stream_status()
+    Uref = O.moments(f, oracle_grid(N, L, 8))
+    assert np.max(np.abs(U.cpu().numpy() - Uref) / np.abs(Uref).max(axis=1, keepdims=True)) < 1e-13
+
+
+def test_projected_Q_has_zero_moments():
+    N, L, M = 32, 8.0, 64
+    f = W.two_maxwellians(2, N, L, seed=31)
+    with B.Grid(N, L, 1.0, M) as g:
+        for prec in (B.BOLTZ_FP64, B.BOLTZ_FP32_FFT):
+            Q = torch.from_numpy(run_collide(g, f, prec)).cuda()
+            U = torch.empty(2, 5, dtype=torch.float64, device="cuda")
+            B.boltz_moments(g.batch(2), Q, U)
+            UA = torch.empty(2, 5, dtype=torch.float64, device="cuda")
+            B.boltz_moments(g.batch(2), Q.abs(), UA)
+            assert (U.abs() / UA[:, :1]).max().item() < 1e-13
+
+
+@pytest.mark.parametrize("rk", [1, 2])
+def test_relax_parity(rk):
+    N, L, M = 16, 6.0, 16
+    f = W.two_maxwellians(3, N, L, seed=44)
+    og = oracle_grid(N, L, M)
+    ref = O.relax(f, og, 0.004, 3, rk_order=rk)
+    with B.Grid(N, L, 1.0, M) as g:
+        ft = torch.from_numpy(f).cuda()
+        B.boltz_relax(g.batch(3), ft, 0.004, 3, rk)
+        B.boltz_stream_status()
+        out = ft.cpu().numpy()
+        assert rel_l2(out - f, ref - f) <= 1e-11
+        ft32 = torch.from_numpy(f).cuda()
+        B.boltz_relax(g.batch(3, B.BOLTZ_FP32_FFT), ft32, 0.004, 3, rk)
+        B.boltz_stream_status()
+        assert rel_l2(ft32.cpu().numpy() - f, ref - f) <= fp32_tol(f, og)
+        # moments held at their initial values (float64 master copy)
+        U0 = O.moments(f, og)
+        assert np.max(np.abs(O.moments(ft32.cpu().numpy(), og) - U0) / np.abs(U0).max(axis=1, keepdims=True)) < 1e-13
+
+
+def test_empty_batch_and_zero_steps():
+    with B.Grid(16, 6.0, 1.0, 8) as g:
+        B.boltz_collide(g.batch(0), 0, 0)
+        f = torch.zeros(1, 16, 16, 16, dtype=torch.float64, device="cuda")
+        B.boltz_relax(g.batch(1), f, 0.1, 0)
+        B.boltz_stream_status()
+
+
+def test_nonfinite_input_is_reported():
+    with B.Grid(16, 6.0, 1.0, 8) as g:
+        f = torch.from_numpy(W.two_maxwellians(2, 16, 6.0, seed=1)).cuda()
+        f[1, 3, 4, 5] = float("nan")
+        Q = torch.empty_like(f)
+        B.boltz_collide(g.batch(2), f, Q)
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_stream_status()
+        assert ei.value.status == B.BOLTZ_ENONFINITE
+        assert torch.isfinite(Q[0]).all()          # the other cell is untouched by the NaN
+        B.boltz_stream_status()                    # status was cleared
+
+
+def test_argument_errors():
+    with B.Grid(16, 6.0, 1.0, 8) as g:
+        f = torch.zeros(2, 16, 16, 16, dtype=torch.float64, device="cuda")
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_collide(g.batch(2), f, f)
+        assert ei.value.status == B.BOLTZ_EINVAL
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_relax(g.batch(2), f, -0.1, 1)
+        assert ei.value.status == B.BOLTZ_EINVAL
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_collide(g.batch(2, B.BOLTZ_TF32_DFT), f, torch.empty_like(f))
+        assert ei.value.status == B.BOLTZ_EUNSUPPORTED
+
+
+def test_full_size_fp64_sampled():
+    """4096 cells x 32^3, M = 64, FP64, the configuration the plain form is timed on;
+    sampled cells against the oracle plus exact per-cell properties on all cells."""
+    n_cells, N, L, M, seed = 4096, 32, 8.0, 64, 20162
+    with B.Grid(N, L, 1.0, M) as g:
+        f = torch.empty(n_cells, N, N, N, dtype=torch.float64)
+        for c0 in range(0, n_cells, 512):
+            f[c0:c0 + 512] = torch.from_numpy(W.two_maxwellians(n_cells, N, L, seed, cells=range(c0, c0 + 512)))
+        fd = f.cuda()
+        Q = torch.empty_like(fd)
+        B.boltz_collide(g.batch(n_cells), fd, Q)
+        B.boltz_stream_status()
+        U = torch.empty(n_cells, 5, dtype=torch.float64, device="cuda")
+        B.boltz_moments(g.batch(n_cells), Q, U)
+        UA = torch.empty(n_cells, 5, dtype=torch.float64, device="cuda")
+        B.boltz_moments(g.batch(n_cells), Q.abs(), UA)
+        assert (U.abs() / UA[:, :1]).max().item() < 1e-13
+        sample = [0, 1, 2047, 4095]
+        Qref = O.collide(W.two_maxwellians(n_cells, N, L, seed, cells=sample), oracle_grid(N, L, M))
+        assert rel_l2(Q[sample].cpu().numpy(), Qref) <= 1e-12
