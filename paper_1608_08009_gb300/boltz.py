@@ -33,7 +33,7 @@ _STATUS_NAMES = {0: "BOLTZ_OK", 1: "BOLTZ_EINVAL", 2: "BOLTZ_ENOMEM", 3: "BOLTZ_
 
 EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "boltz_collide",
             "boltz_relax", "boltz_moments", "boltz_stream_status", "boltz_last_error",
-            "boltz_grid_info", "boltz_grid_tables", "boltz_version")
+            "boltz_grid_info", "boltz_grid_tables", "boltz_version", "boltz_relax_noalloc")
 
 
 class BoltzError(RuntimeError):
@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_collide.argtypes = [P(boltz_batch), vp, vp, vp]
         L.boltz_relax.argtypes = [P(boltz_batch), vp, f64, i32, i32, vp]
         L.boltz_moments.argtypes = [P(boltz_batch), vp, vp, vp]
+        L.boltz_relax_noalloc.argtypes = [P(boltz_batch), vp, f64, i32, vp]
         L.boltz_stream_status.argtypes = [vp]
         L.boltz_last_error.argtypes = []
         L.boltz_last_error.restype = ctypes.c_char_p
@@ -80,7 +81,8 @@ def lib() -> ctypes.CDLL:
         L.boltz_version.argtypes = []
         L.boltz_version.restype = ctypes.c_char_p
         for name in ("boltz_create_grid", "boltz_destroy_grid", "boltz_collide", "boltz_relax",
-                     "boltz_moments", "boltz_stream_status", "boltz_grid_info", "boltz_grid_tables"):
+                     "boltz_moments", "boltz_stream_status", "boltz_grid_info", "boltz_grid_tables",
+                     "boltz_relax_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -135,6 +137,11 @@ def boltz_collide(batch: boltz_batch, f, Q, stream=None) -> None:
 
 def boltz_relax(batch: boltz_batch, f, dt: float, steps: int, rk_order: int = 1, stream=None) -> None:
     _check(lib().boltz_relax(ctypes.byref(batch), _ptr(f), dt, steps, rk_order, _stream(stream)))
+
+
+def boltz_relax_noalloc(batch: boltz_batch, f, dt: float, steps: int, stream=None) -> None:
+    """Forward-Euler relaxation with no allocation (scratch in a fixed device array)."""
+    _check(lib().boltz_relax_noalloc(ctypes.byref(batch), _ptr(f), dt, steps, _stream(stream)))
 
 
 def boltz_moments(batch: boltz_batch, f, U, stream=None) -> None:
