@@ -178,7 +178,7 @@ boltz_status boltz_collide(const boltz_batch* b, const void* f, void* Q, void* s
     return BOLTZ_EINVAL;
   }
   if ((st = check_device(b->grid)) != BOLTZ_OK) return st;
-  return boltz::launch_collide(b->grid, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, Q, 0.0, 0.0, 1.0, nullptr,
+  return boltz::launch_collide(b->grid, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, Q, 0.0, 0.0, 1.0, nullptr, 0,
                                b->grid->project, (cudaStream_t)stream);
 }
 
@@ -247,19 +247,20 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
     }
     g->stage_cap = stage_bytes;
   }
-  // targets: Phi-sums of the initial state (Eq. minim1 with U fixed)
-  st = boltz::launch_phisums(g, b->n_cells, b->f_is_fp64, f, g->U0, 1.0, s);
-  if (st != BOLTZ_OK) return st;
+  // Targets: Phi-sums of the initial state (Eq. minim1 with U fixed), computed by the
+  // first launch from the values it loads anyway and kept in g->U0 for the later ones.
   for (int it = 0; it < steps; ++it) {
+    const int first = (it == 0) ? 1 : 0;
     if (rk_order == 1) {
-      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, g->U0, 1, s);
+      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, g->U0, first, 1,
+                                 s);
       if (st != BOLTZ_OK) return st;
     } else {
       st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, g->stage, 0.0, 1.0, dt, g->U0,
-                                 1, s);
+                                 first, 1, s);
       if (st != BOLTZ_OK) return st;
       st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, g->stage, f, f, 0.5, 0.5, 0.5 * dt, g->U0,
-                                 1, s);
+                                 0, 1, s);
       if (st != BOLTZ_OK) return st;
     }
   }

@@ -47,14 +47,19 @@ struct CollideArgs {
   const void* f_in;    // [cells][N^3] TIO
   const void* f_base;  // [cells][N^3] TIO or null
   void* out;           // [cells][N^3] TIO
-  const void* tab;     // [(M_eff + 1) * N^3] (alpha, alpha') as Vec2<T>; last entry (D, 0)
+  const void* tab;     // [(M_eff + 1)][ky][kx][kz] (alpha, alpha') as Vec2<T>; entry M_eff = (D, 0)
   const double* w;     // [M_eff]
-  const double* Utgt;  // [cells][5] target Phi-sums, or null (target 0)
+  double* Utgt;        // [cells][5] target Phi-sums, or null (target 0)
   double a, b, s;      // out = Pi(a f_base + b f_in + s Q)
   int M_eff;
   int project;
+  int compute_targets; // 1: targets = Phi f_in, computed here and written to Utgt if non-null
   KernelGeom geom;
 };
+
+// Status bits of g_boltz_status.
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;
 
 template <typename T, int N, int C>
 struct CollideCfg {
@@ -63,10 +68,24 @@ struct CollideCfg {
   static constexpr int ROW = N + 1;         // padded row of the x-plane buffer
   static constexpr int WARPS = THREADS / 32;
   using T2 = typename Vec2<T>::type;
-  static constexpr size_t FH = (size_t)N * NP * N;   // spectrum slab [kx][kyl][kz]
-  static constexpr size_t XB = (size_t)NP * N * ROW; // x-plane buffer [xl][ky][kz|z]
-  static constexpr size_t SMEM = (FH + XB) * sizeof(T2) + (size_t)(WARPS + 1) * 5 * sizeof(double);
+  // float32: the spectrum pencil of each thread stays in registers and the x-plane
+  // buffer is double-buffered (one cluster barrier per direction); float64 (register
+  // bound) keeps the spectrum in shared memory with a single x-plane buffer.
+  static constexpr bool kRegSpec = sizeof(T) == 4;
+  static constexpr int NXB = kRegSpec ? 2 : 1;
+  static constexpr size_t FH = kRegSpec ? 0 : (size_t)N * NP * N;  // spectrum slab [kx][kyl][kz]
+  static constexpr size_t XB = (size_t)NP * N * ROW;                // x-plane buffer [xl][ky][kz|z]
+  static constexpr size_t TB = (size_t)NP * N * N;                  // table slab [kyl][kx][kz]
+  static constexpr size_t TB_BYTES = TB * sizeof(T2);
+  static constexpr size_t OFF_XB = FH * sizeof(T2);
+  static constexpr size_t OFF_TB = OFF_XB + NXB * XB * sizeof(T2);
+  static constexpr size_t OFF_RED = OFF_TB + TB_BYTES;
+  // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA
+  static constexpr size_t OFF_MBAR = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  static constexpr size_t SMEM = OFF_MBAR + 16;
   static_assert(THREADS % 32 == 0, "whole warps");
+  static_assert(OFF_TB % 16 == 0 && TB_BYTES % 16 == 0, "bulk copies need 16-byte alignment");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
 template <int C>
@@ -93,6 +112,43 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Bulk asynchronous copy of `bytes` (multiple of 16) from global memory into this CTA's
+// shared memory, completing on the mbarrier at `mbar` (expect_tx set by the caller).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+
+// Thread 0: arm the mbarrier for `bytes` and copy one table slab (chunks of <= 16 KiB).
+__device__ __forceinline__ void load_table_slab(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+  const uint32_t chunk = 16384;
+  for (uint32_t off = 0; off < bytes; off += chunk) {
+    const uint32_t nb = (bytes - off < chunk) ? (bytes - off) : chunk;
+    bulk_copy_g2s(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, nb, mbar);
+  }
+}
+
+// Bounded wait for the phase `parity` of the mbarrier.  Returns false (and flags the
+// device status) if the copy did not complete within the iteration limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  atomicOr(&g_boltz_status, kStatusTimeout);
+  return false;
+}
+
 template <typename T, typename TIO, int N, int C>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, 1)
 collide_kernel(const CollideArgs args) {
@@ -100,36 +156,79 @@ collide_kernel(const CollideArgs args) {
   using T2 = typename Cfg::T2;
   constexpr int NP = Cfg::NP, ROW = Cfg::ROW, WARPS = Cfg::WARPS;
   constexpr int n = N * N * N;
+  constexpr bool kRegSpec = Cfg::kRegSpec;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* Fh = reinterpret_cast<T2*>(smem_raw);
-  T2* XB = Fh + Cfg::FH;
-  double* red = reinterpret_cast<double*>(XB + Cfg::XB);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T2* Fh = reinterpret_cast<T2*>(smem_raw);                       // unused when kRegSpec
+  T2* XB0 = reinterpret_cast<T2*>(smem_raw + Cfg::OFF_XB);
+  T2* TB = reinterpret_cast<T2*>(smem_raw + Cfg::OFF_TB);
+  double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::OFF_MBAR);
 
   const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const long long cell = blockIdx.x / C;
   const int t = threadIdx.x;
   const int tA = t / N, tB = t % N;
   const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  // this CTA's ky-slab of direction j: tab + j n + rank NP N N, contiguous
+  const size_t slab_off = (size_t)rank * NP * N * N;
+
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    load_table_slab(TB, tab + slab_off, (uint32_t)Cfg::TB_BYTES, mbar);  // direction 0
+  }
+  uint32_t phase = 0;
+  bool tb_pending = true;   // a table slab is being copied into TB
+  bool timed_out = false;
 
   T re[N], im[N];
+  T fr[kRegSpec ? N : 1], fi[kRegSpec ? N : 1];  // spectrum pencil (kRegSpec)
 
+  const double L = args.geom.L, dv = args.geom.dv;
+  const int lane = t & 31, warp = t >> 5;
   // ---- forward transform, pass along y: thread (x = rank NP + tA, z = tB) ----------
   {
     const int x = rank * NP + tA;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // sum_y f, sum_y y f, sum_y y^2 f (targets)
 #pragma unroll
     for (int y = 0; y < N; ++y) {
-      re[y] = (T)fin[(x * N + y) * N + tB];
+      const TIO fv = fin[(x * N + y) * N + tB];
+      re[y] = (T)fv;
       im[y] = T(0);
+      if (args.compute_targets) {
+        s0 += (double)fv;
+        s1 += (double)y * (double)fv;
+        s2 += (double)(y * y) * (double)fv;
+      }
+    }
+    if (args.compute_targets) {
+      // Phi f over this thread's y-row: v_y = -L + y dv
+      const double vx = -L + x * dv, vz = -L + tB * dv;
+      const double sy = -L * s0 + dv * s1;                              // sum v_y f
+      const double syy = L * L * s0 - 2.0 * L * dv * s1 + dv * dv * s2;  // sum v_y^2 f
+      double m[5] = {s0, vx * s0, sy, vz * s0, 0.5 * ((vx * vx + vz * vz) * s0 + syy)};
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const double v = warp_sum(m[r]);
+        if (lane == 0) red[warp * 5 + r] = v;
+      }
     }
     fft_regs<N, -1>(re, im);
 #pragma unroll
-    for (int k = 0; k < N; ++k) XB[(tA * N + k) * ROW + tB] = mk2<T>(re[k], im[k]);
+    for (int k = 0; k < N; ++k) XB0[(tA * N + k) * ROW + tB] = mk2<T>(re[k], im[k]);
   }
   __syncthreads();
+  if (args.compute_targets && t < 5) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w * 5 + t];
+    red[(WARPS + 1) * 5 + t] = v;  // this CTA's Phi f_in
+  }
   // ---- pass along z: thread (xl = tA, ky = tB) ---------------------------------------
   {
-    T2* row = XB + (tA * N + tB) * ROW;
+    T2* row = XB0 + (tA * N + tB) * ROW;
 #pragma unroll
     for (int z = 0; z < N; ++z) {
       const T2 v = row[z];
@@ -146,7 +245,7 @@ collide_kernel(const CollideArgs args) {
     const int ky = rank * NP + tA;
 #pragma unroll
     for (int x = 0; x < N; ++x) {
-      const T2 v = cta_smem<C>(XB, x / NP)[((x % NP) * N + ky) * ROW + tB];
+      const T2 v = cta_smem<C>(XB0, x / NP)[((x % NP) * N + ky) * ROW + tB];
       re[x] = v.x;
       im[x] = v.y;
     }
@@ -157,25 +256,40 @@ collide_kernel(const CollideArgs args) {
     for (int kx = 0; kx < N; ++kx) {
       // Every mode with a component -N/2 is removed so each inverse transform is real.
       const bool z0 = nyq || (kx == N / 2);
-      Fh[(kx * NP + tA) * N + tB] = z0 ? mk2<T>(T(0), T(0)) : mk2<T>(re[kx] * scale, im[kx] * scale);
+      const T vr = z0 ? T(0) : re[kx] * scale, vi = z0 ? T(0) : im[kx] * scale;
+      if constexpr (kRegSpec) {
+        fr[kx] = vr;
+        fi[kx] = vi;
+      } else {
+        Fh[(kx * NP + tA) * N + tB] = mk2<T>(vr, vi);
+      }
     }
   }
-  cluster_barrier<C>();
+  if constexpr (!kRegSpec) cluster_barrier<C>();  // single buffer: peers done reading it
 
   // ---- angular loop: one complex inverse transform per separated term --------------
   T acc[N];
 #pragma unroll
   for (int y = 0; y < N; ++y) acc[y] = T(0);
-  const T2* tab = reinterpret_cast<const T2*>(args.tab);
-  const int M_eff = args.M_eff;
   for (int j = 0; j <= M_eff; ++j) {
+    T2* XB = XB0 + (kRegSpec ? ((j + 1) & 1) * Cfg::XB : 0);
+    if (tb_pending) {
+      timed_out |= !mbar_wait(mbar, phase);
+      phase ^= 1u;
+      tb_pending = false;
+    }
     {  // pass along kx with the coefficients: thread (kyl = tA, kz = tB)
       const int ky = rank * NP + tA;
-      const T2* tj = tab + (size_t)j * n + ky * N + tB;
+      const T2* tj = TB + tA * N * N + tB;
 #pragma unroll
       for (int kx = 0; kx < N; ++kx) {
-        const T2 c = Fh[(kx * NP + tA) * N + tB];
-        const T2 ab = __ldg(tj + kx * N * N);
+        T2 c;
+        if constexpr (kRegSpec) {
+          c = mk2<T>(fr[kx], fi[kx]);
+        } else {
+          c = Fh[(kx * NP + tA) * N + tB];
+        }
+        const T2 ab = tj[kx * N];
         re[kx] = ab.x * c.x - ab.y * c.y;
         im[kx] = ab.x * c.y + ab.y * c.x;
       }
@@ -184,6 +298,10 @@ collide_kernel(const CollideArgs args) {
       for (int x = 0; x < N; ++x) cta_smem<C>(XB, x / NP)[((x % NP) * N + ky) * ROW + tB] = mk2<T>(re[x], im[x]);
     }
     cluster_barrier<C>();
+    if (j < M_eff) {  // every thread of this CTA is done with the table slab: fetch the next
+      if (t == 0) load_table_slab(TB, tab + (size_t)(j + 1) * n + slab_off, (uint32_t)Cfg::TB_BYTES, mbar);
+      tb_pending = true;
+    }
     {  // pass along kz: thread (xl = tA, ky = tB)
       T2* row = XB + (tA * N + tB) * ROW;
 #pragma unroll
@@ -212,12 +330,13 @@ collide_kernel(const CollideArgs args) {
       }
       // for j == M_eff, re[] now holds the loss multiplier L(v) along y
     }
-    if (j < M_eff) cluster_barrier<C>();
+    if constexpr (!kRegSpec) {
+      if (j < M_eff) cluster_barrier<C>();  // single buffer: owners done before the next scatter
+    }
   }
 
   // ---- Q = Q+ - f L, projection and update (float64) ---------------------------------
   const int x = rank * NP + tA;
-  const double L = args.geom.L, dv = args.geom.dv;
   const double vx = -L + x * dv, vz = -L + tB * dv;
   const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
   double g[N];
@@ -226,8 +345,8 @@ collide_kernel(const CollideArgs args) {
   for (int y = 0; y < N; ++y) {
     const int idx = (x * N + y) * N + tB;
     const TIO fv = fin[idx];
-    const T q = acc[y] - (T)fv * re[y];
-    double gv = args.s * (double)q;
+    const double q = (double)acc[y] - (double)fv * (double)re[y];
+    double gv = args.s * q;
     if (args.b != 0.0) gv += args.b * (double)fv;
     if (fb) gv += args.a * (double)fb[idx];
     g[y] = gv;
@@ -238,7 +357,6 @@ collide_kernel(const CollideArgs args) {
     m[3] += gv * vz;
     m[4] += gv * (0.5 * (vx * vx + vy * vy + vz * vz));
   }
-  const int lane = t & 31, warp = t >> 5;
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     const double s = warp_sum(m[r]);
@@ -253,15 +371,23 @@ collide_kernel(const CollideArgs args) {
   cluster_barrier<C>();
   double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (args.project) {
-    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int q = 0; q < C; ++q) {
       const double* p = cta_smem<C>(red + WARPS * 5, q);
 #pragma unroll
-      for (int r = 0; r < 5; ++r) tot[r] += p[r];
+      for (int r = 0; r < 5; ++r) {
+        tot[r] += p[r];
+        if (args.compute_targets) tgt[r] += p[5 + r];
+      }
     }
+    if (!args.compute_targets && args.Utgt) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
+    }
+    if (args.compute_targets && args.Utgt && rank == 0 && t < 5) args.Utgt[cell * 5 + t] = tgt[t];
     double rhs[5];
 #pragma unroll
-    for (int r = 0; r < 5; ++r) rhs[r] = (args.Utgt ? args.Utgt[cell * 5 + r] : 0.0) - tot[r];
+    for (int r = 0; r < 5; ++r) rhs[r] = tgt[r] - tot[r];
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
       double s = 0.0;
@@ -281,10 +407,15 @@ collide_kernel(const CollideArgs args) {
     bad |= !isfinite(val);
     out[(x * N + y) * N + tB] = (TIO)val;
   }
-  if (bad) atomicOr(&g_boltz_status, 1u);
+  if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
+  // A copy can only still be in flight if a wait gave up: wait once more (bounded).
+  if (timed_out) mbar_wait(mbar, phase ^ 1u);
 }
 
-// Plain sums Phi f per cell, scaled: U[c][r] = scale * sum_v phi_r(v) f(v).
+// Plain sums Phi f per cell, scaled: U[c][r] = scale * sum_v phi_r(v) f(v).  One thread
+// per (x, y) row: sum f, sum z f and sum z^2 f along the row, then the row's share of the
+// five moments from v_z = -L + z dv (float64 throughout; three float64 operations per
+// value instead of one per moment).
 template <typename TIO>
 __global__ void __launch_bounds__(256) phisums_kernel(const TIO* f, double* U, int N, double L, double dv,
                                                       double scale) {
@@ -292,15 +423,24 @@ __global__ void __launch_bounds__(256) phisums_kernel(const TIO* f, double* U, i
   const int n = N * N * N;
   const TIO* fc = f + cell * n;
   double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int x = idx / (N * N), y = (idx / N) % N, z = idx % N;
-    const double vx = -L + x * dv, vy = -L + y * dv, vz = -L + z * dv;
-    const double fv = (double)fc[idx];
-    m[0] += fv;
-    m[1] += fv * vx;
-    m[2] += fv * vy;
-    m[3] += fv * vz;
-    m[4] += fv * (0.5 * (vx * vx + vy * vy + vz * vz));
+  for (int row = threadIdx.x; row < N * N; row += blockDim.x) {
+    const int x = row / N, y = row % N;
+    const TIO* r = fc + (size_t)row * N;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int z = 0; z < N; ++z) {
+      const double fv = (double)r[z];
+      s0 += fv;
+      s1 += (double)z * fv;
+      s2 += (double)(z * z) * fv;
+    }
+    const double vx = -L + x * dv, vy = -L + y * dv;
+    const double sz = -L * s0 + dv * s1;
+    const double szz = L * L * s0 - 2.0 * L * dv * s1 + dv * dv * s2;
+    m[0] += s0;
+    m[1] += vx * s0;
+    m[2] += vy * s0;
+    m[3] += sz;
+    m[4] += 0.5 * ((vx * vx + vy * vy) * s0 + szz);
   }
   __shared__ double red[8][5];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -354,16 +494,19 @@ boltz_status upload_tables(boltz_grid_s* g) {
     set_error("host staging of the device tables failed");
     return BOLTZ_ENOMEM;
   }
-  for (int i = 0; i < g->M_eff; ++i)
-    for (size_t k = 0; k < n; ++k) {
-      const double a = g->alpha[(size_t)i * n + k], b = g->alphap[(size_t)i * n + k];
-      h64[(size_t)i * n + k] = make_double2(a, b);
-      h32[(size_t)i * n + k] = make_float2((float)a, (float)b);
-    }
-  for (size_t k = 0; k < n; ++k) {
-    h64[(size_t)g->M_eff * n + k] = make_double2(g->D[k], 0.0);
-    h32[(size_t)g->M_eff * n + k] = make_float2((float)g->D[k], 0.0f);
-  }
+  // device layout [i][ky][kx][kz]: the ky-slab of one direction is one contiguous block
+  const int N = g->N;
+  for (int i = 0; i <= g->M_eff; ++i)
+    for (int kx = 0; kx < N; ++kx)
+      for (int ky = 0; ky < N; ++ky)
+        for (int kz = 0; kz < N; ++kz) {
+          const size_t src = ((size_t)kx * N + ky) * N + kz;
+          const size_t dst = (size_t)i * n + ((size_t)ky * N + kx) * N + kz;
+          const double a = (i < g->M_eff) ? g->alpha[(size_t)i * n + src] : g->D[src];
+          const double b = (i < g->M_eff) ? g->alphap[(size_t)i * n + src] : 0.0;
+          h64[dst] = make_double2(a, b);
+          h32[dst] = make_float2((float)a, (float)b);
+        }
   if ((e = cudaMalloc(&g->tab64, entries * sizeof(double2))) != cudaSuccess) {
     set_error(std::string("device tables: ") + cudaGetErrorString(e));
     return BOLTZ_ENOMEM;
@@ -426,8 +569,8 @@ static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int6
 }
 
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, const void* f_in,
-                            const void* f_base, void* out, double a, double b, double s, const double* Utgt,
-                            int project, cudaStream_t stream) {
+                            const void* f_base, void* out, double a, double b, double s, double* Utgt,
+                            int compute_targets, int project, cudaStream_t stream) {
   if (n_cells == 0) return BOLTZ_OK;
   if (!collide_supported(g->N, prec)) {
     set_error("unsupported (N, precision) combination");
@@ -444,6 +587,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.s = s;
   args.M_eff = g->M_eff;
   args.project = project;
+  args.compute_targets = compute_targets;
   args.geom.L = g->L;
   args.geom.dv = g->dv;
   for (int i = 0; i < 25; ++i) args.geom.G[i] = g->proj.G[i];

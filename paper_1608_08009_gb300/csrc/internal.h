@@ -55,9 +55,13 @@ boltz_status build_tables(boltz_grid_s* g);
 
 // Kernel launchers (collide.cu).
 boltz_status upload_tables(boltz_grid_s* g);
+// out = Pi(a f_base + b f_in + s Q(f_in)).  Pi projects onto the targets Utgt (Phi-sums,
+// [cells][5]); compute_targets = 1 takes the targets from f_in itself (and stores them to
+// Utgt when non-null), 0 reads Utgt (null: target 0, i.e. the projection of Q).
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64,
                             const void* f_in, const void* f_base, void* out, double a, double b,
-                            double s, const double* Utgt, int project, cudaStream_t stream);
+                            double s, double* Utgt, int compute_targets, int project,
+                            cudaStream_t stream);
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
                             double* U, double scale, cudaStream_t stream);
 bool collide_supported(int N, int prec);
