@@ -65,7 +65,9 @@ template <typename T, int N, int C>
 struct CollideCfg {
   static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
   static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
-  static constexpr int ROW = N + 1;         // padded row of the x-plane buffer
+  // padded row of the x-plane buffer: conflict-free row-wise 16-byte accesses (float2
+  // rows padded to a multiple of 16 bytes) and column-wise accesses
+  static constexpr int ROW = sizeof(T) == 4 ? N + 2 : N + 1;
   static constexpr int WARPS = THREADS / 32;
   using T2 = typename Vec2<T>::type;
   // float32: the spectrum pencil of each thread stays in registers and the x-plane
@@ -114,6 +116,62 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared::cluster address of `addr` (a shared::cta address) in the CTA of rank r
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t r) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(r));
+  return out;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double2 v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" :: "r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ float2 ld_cluster_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ double2 ld_cluster_d2(uint32_t a) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
+}
+template <typename T2> __device__ __forceinline__ T2 ld_cluster(uint32_t a);
+template <> __device__ __forceinline__ float2 ld_cluster<float2>(uint32_t a) { return ld_cluster_f2(a); }
+template <> __device__ __forceinline__ double2 ld_cluster<double2>(uint32_t a) { return ld_cluster_d2(a); }
+
+// Row of N complex values: 16-byte vector accesses for float2 (two values per access).
+template <int N>
+__device__ __forceinline__ void load_row(const float2* row, float (&re)[N], float (&im)[N]) {
+  const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    const float4 v = r4[i];
+    re[2 * i] = v.x; im[2 * i] = v.y; re[2 * i + 1] = v.z; im[2 * i + 1] = v.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void load_row(const double2* row, double (&re)[N], double (&im)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double2 v = row[i];
+    re[i] = v.x; im[i] = v.y;
+  }
+}
+template <int N>
+__device__ __forceinline__ void store_row(float2* row, const float (&re)[N], const float (&im)[N]) {
+  float4* r4 = reinterpret_cast<float4*>(row);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) r4[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+}
+template <int N>
+__device__ __forceinline__ void store_row(double2* row, const double (&re)[N], const double (&im)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) row[i] = make_double2(re[i], im[i]);
 }
 
 // Bulk asynchronous copy of `bytes` (multiple of 16) from global memory into this CTA's
@@ -229,15 +287,9 @@ collide_kernel(const CollideArgs args) {
   // ---- pass along z: thread (xl = tA, ky = tB) ---------------------------------------
   {
     T2* row = XB0 + (tA * N + tB) * ROW;
-#pragma unroll
-    for (int z = 0; z < N; ++z) {
-      const T2 v = row[z];
-      re[z] = v.x;
-      im[z] = v.y;
-    }
+    load_row<N>(row, re, im);
     fft_regs<N, -1>(re, im);
-#pragma unroll
-    for (int k = 0; k < N; ++k) row[k] = mk2<T>(re[k], im[k]);
+    store_row<N>(row, re, im);
   }
   cluster_barrier<C>();
   // ---- pass along x (remote x-planes): thread (kyl = tA, kz = tB) --------------------
@@ -245,7 +297,12 @@ collide_kernel(const CollideArgs args) {
     const int ky = rank * NP + tA;
 #pragma unroll
     for (int x = 0; x < N; ++x) {
-      const T2 v = cta_smem<C>(XB0, x / NP)[((x % NP) * N + ky) * ROW + tB];
+      T2 v;
+      if constexpr (C > 1) {
+        v = ld_cluster<T2>(cluster_addr(smem_u32(XB0 + ((x % NP) * N + ky) * ROW + tB), x / NP));
+      } else {
+        v = XB0[(x * N + ky) * ROW + tB];
+      }
       re[x] = v.x;
       im[x] = v.y;
     }
@@ -273,6 +330,7 @@ collide_kernel(const CollideArgs args) {
   for (int y = 0; y < N; ++y) acc[y] = T(0);
   for (int j = 0; j <= M_eff; ++j) {
     T2* XB = XB0 + (kRegSpec ? ((j + 1) & 1) * Cfg::XB : 0);
+    const T wj = (j < M_eff) ? (T)args.w[j] : T(0);  // issued early, used after the passes
     if (tb_pending) {
       timed_out |= !mbar_wait(mbar, phase);
       phase ^= 1u;
@@ -294,8 +352,19 @@ collide_kernel(const CollideArgs args) {
         im[kx] = ab.x * c.y + ab.y * c.x;
       }
       fft_regs<N, +1>(re, im);
+      if constexpr (C > 1) {
+        const uint32_t mine = smem_u32(XB + ky * ROW + tB);
 #pragma unroll
-      for (int x = 0; x < N; ++x) cta_smem<C>(XB, x / NP)[((x % NP) * N + ky) * ROW + tB] = mk2<T>(re[x], im[x]);
+        for (int q = 0; q < C; ++q) {
+          const uint32_t dst = cluster_addr(mine, q);
+#pragma unroll
+          for (int xl = 0; xl < NP; ++xl)
+            st_cluster(dst + (uint32_t)(xl * N * ROW * sizeof(T2)), mk2<T>(re[q * NP + xl], im[q * NP + xl]));
+        }
+      } else {
+#pragma unroll
+        for (int x = 0; x < N; ++x) XB[(x * N + ky) * ROW + tB] = mk2<T>(re[x], im[x]);
+      }
     }
     cluster_barrier<C>();
     if (j < M_eff) {  // every thread of this CTA is done with the table slab: fetch the next
@@ -304,15 +373,9 @@ collide_kernel(const CollideArgs args) {
     }
     {  // pass along kz: thread (xl = tA, ky = tB)
       T2* row = XB + (tA * N + tB) * ROW;
-#pragma unroll
-      for (int z = 0; z < N; ++z) {
-        const T2 v = row[z];
-        re[z] = v.x;
-        im[z] = v.y;
-      }
+      load_row<N>(row, re, im);
       fft_regs<N, +1>(re, im);
-#pragma unroll
-      for (int z = 0; z < N; ++z) row[z] = mk2<T>(re[z], im[z]);
+      store_row<N>(row, re, im);
     }
     __syncthreads();
     {  // pass along ky: thread (xl = tA, z = tB); outputs along y
@@ -324,7 +387,6 @@ collide_kernel(const CollideArgs args) {
       }
       fft_regs<N, +1>(re, im);
       if (j < M_eff) {
-        const T wj = (T)args.w[j];
 #pragma unroll
         for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
       }
@@ -340,23 +402,23 @@ collide_kernel(const CollideArgs args) {
   const double vx = -L + x * dv, vz = -L + tB * dv;
   const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
   double g[N];
-  double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;  // sum_y g, sum_y y g, sum_y y^2 g over this row
 #pragma unroll
   for (int y = 0; y < N; ++y) {
     const int idx = (x * N + y) * N + tB;
     const TIO fv = fin[idx];
-    const double q = (double)acc[y] - (double)fv * (double)re[y];
-    double gv = args.s * q;
+    const T q = acc[y] - (T)fv * re[y];  // Q = Q+ - f L (one rounding in T)
+    double gv = args.s * (double)q;
     if (args.b != 0.0) gv += args.b * (double)fv;
     if (fb) gv += args.a * (double)fb[idx];
     g[y] = gv;
-    const double vy = -L + y * dv;
-    m[0] += gv;
-    m[1] += gv * vx;
-    m[2] += gv * vy;
-    m[3] += gv * vz;
-    m[4] += gv * (0.5 * (vx * vx + vy * vy + vz * vz));
+    S0 += gv;
+    S1 += (double)y * gv;
+    S2 += (double)(y * y) * gv;
   }
+  // Phi g over the row, with v_y = -L + y dv
+  double m[5] = {S0, vx * S0, -L * S0 + dv * S1, vz * S0,
+                 0.5 * ((vx * vx + vz * vz + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2)};
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     const double s = warp_sum(m[r]);
@@ -399,11 +461,13 @@ collide_kernel(const CollideArgs args) {
   cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
   TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
   bool bad = false;
-  const double base = c5[0] + c5[1] * vx + c5[3] * vz;
+  // Phi^T c at (vx, vy, vz) as a quadratic in the row index y: P0 + P1 y + P2 y^2
+  const double P0 = c5[0] + c5[1] * vx + c5[3] * vz + 0.5 * c5[4] * (vx * vx + vz * vz + L * L) - c5[2] * L;
+  const double P1 = (c5[2] - c5[4] * L) * dv;
+  const double P2 = 0.5 * c5[4] * dv * dv;
 #pragma unroll
   for (int y = 0; y < N; ++y) {
-    const double vy = -L + y * dv;
-    const double val = g[y] + base + c5[2] * vy + c5[4] * (0.5 * (vx * vx + vy * vy + vz * vz));
+    const double val = g[y] + (P0 + (double)y * (P1 + (double)y * P2));
     bad |= !isfinite(val);
     out[(x * N + y) * N + tB] = (TIO)val;
   }

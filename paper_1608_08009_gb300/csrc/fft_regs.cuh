@@ -42,38 +42,80 @@ struct BitReverse {
   }
 };
 
-// One radix-2 decimation-in-time stage of butterflies of span LEN, then the next stage.
-// LEN is a template parameter so every loop has compile-time bounds and unrolls fully:
-// the register arrays are only ever indexed by constants.
-template <int N, int SIGN, int LEN, typename T>
-__device__ __forceinline__ void fft_stage(T (&xr)[N], T (&xi)[N]) {
-  constexpr int half = LEN / 2;
-  constexpr int stride = 64 / LEN;
+// Complex multiply of (br, bi) by the twiddle exp(SIGN 2 pi i m / 64), m a compile-time
+// constant after unrolling (m = 0 and m = 16 need no multiplication).
+template <int SIGN, typename T>
+__device__ __forceinline__ void twiddle(int m, T br, T bi, T& tr, T& ti) {
+  if (m == 0) {
+    tr = br; ti = bi;
+  } else if (m == 16) {  // exp(SIGN i pi / 2) = SIGN i
+    tr = (SIGN > 0) ? -bi : bi;
+    ti = (SIGN > 0) ? br : -br;
+  } else if (m == 32) {  // -1
+    tr = -br; ti = -bi;
+  } else if (m == 48) {  // -SIGN i
+    tr = (SIGN > 0) ? bi : -bi;
+    ti = (SIGN > 0) ? -br : br;
+  } else {
+    const T c = tw_cos<T>(m);
+    const T sn = (SIGN > 0) ? tw_sin<T>(m) : -tw_sin<T>(m);
+    tr = br * c - bi * sn;
+    ti = br * sn + bi * c;
+  }
+}
+
+// Decimation-in-time stages on bit-reversed input.  SPAN is the length of the
+// sub-transforms already formed; a radix-4 stage merges four of them (span 4 SPAN,
+// three twiddle multiplications per four points, the inner factor SIGN i is a swap), a
+// radix-2 stage two of them.  Spans are template parameters so every loop has
+// compile-time bounds and unrolls fully: register indices are all constants.
+template <int N, int SIGN, int SPAN, typename T>
+__device__ __forceinline__ void fft_stages(T (&xr)[N], T (&xi)[N]) {
+  if constexpr (SPAN < N) {
+    if constexpr (4 * SPAN <= N) {
+      constexpr int L = 4 * SPAN;
+      constexpr int stride = 64 / L;  // exp(SIGN 2 pi i k / L) = twiddle index k * stride
 #pragma unroll
-  for (int s = 0; s < N; s += LEN) {
+      for (int s = 0; s < N; s += L) {
 #pragma unroll
-    for (int k = 0; k < half; ++k) {
-      const int m = k * stride;  // twiddle exp(SIGN 2 pi i m / 64)
-      const T br = xr[s + k + half], bi = xi[s + k + half];
-      T tr, ti;
-      if (m == 0) {
-        tr = br; ti = bi;
-      } else if (m == 16) {  // exp(SIGN i pi / 2) = SIGN i
-        tr = (SIGN > 0) ? -bi : bi;
-        ti = (SIGN > 0) ? br : -br;
-      } else {
-        const T c = tw_cos<T>(m);
-        const T sn = (SIGN > 0) ? tw_sin<T>(m) : -tw_sin<T>(m);
-        tr = br * c - bi * sn;
-        ti = br * sn + bi * c;
+        for (int k = 0; k < SPAN; ++k) {
+          const int i0 = s + k, i1 = i0 + SPAN, i2 = i1 + SPAN, i3 = i2 + SPAN;
+          T b1r, b1i, b2r, b2i, b3r, b3i;
+          twiddle<SIGN>(2 * k * stride, xr[i1], xi[i1], b1r, b1i);
+          twiddle<SIGN>(k * stride, xr[i2], xi[i2], b2r, b2i);
+          twiddle<SIGN>(3 * k * stride, xr[i3], xi[i3], b3r, b3i);
+          const T t0r = xr[i0] + b1r, t0i = xi[i0] + b1i;
+          const T t1r = xr[i0] - b1r, t1i = xi[i0] - b1i;
+          const T t2r = b2r + b3r, t2i = b2i + b3i;
+          const T t3r = b2r - b3r, t3i = b2i - b3i;
+          // (SIGN i) t3
+          const T u3r = (SIGN > 0) ? -t3i : t3i;
+          const T u3i = (SIGN > 0) ? t3r : -t3r;
+          xr[i0] = t0r + t2r; xi[i0] = t0i + t2i;
+          xr[i2] = t0r - t2r; xi[i2] = t0i - t2i;
+          xr[i1] = t1r + u3r; xi[i1] = t1i + u3i;
+          xr[i3] = t1r - u3r; xi[i3] = t1i - u3i;
+        }
       }
-      xr[s + k + half] = xr[s + k] - tr;
-      xi[s + k + half] = xi[s + k] - ti;
-      xr[s + k] = xr[s + k] + tr;
-      xi[s + k] = xi[s + k] + ti;
+      fft_stages<N, SIGN, 4 * SPAN>(xr, xi);
+    } else {
+      constexpr int L = 2 * SPAN;
+      constexpr int stride = 64 / L;
+#pragma unroll
+      for (int s = 0; s < N; s += L) {
+#pragma unroll
+        for (int k = 0; k < SPAN; ++k) {
+          T tr, ti;
+          twiddle<SIGN>(k * stride, xr[s + k + SPAN], xi[s + k + SPAN], tr, ti);
+          xr[s + k + SPAN] = xr[s + k] - tr;
+          xi[s + k + SPAN] = xi[s + k] - ti;
+          xr[s + k] = xr[s + k] + tr;
+          xi[s + k] = xi[s + k] + ti;
+        }
+      }
+      fft_stages<N, SIGN, 2 * SPAN>(xr, xi);
     }
   }
-  if constexpr (LEN < N) fft_stage<N, SIGN, 2 * LEN>(xr, xi);
 }
 
 // x_k <- sum_j x_j exp(SIGN 2 pi i j k / N); no scaling.  SIGN = -1 forward, +1 inverse.
@@ -89,7 +131,19 @@ __device__ __forceinline__ void fft_regs(T (&xr)[N], T (&xi)[N]) {
       t = xi[i]; xi[i] = xi[j]; xi[j] = t;
     }
   }
-  fft_stage<N, SIGN, 2>(xr, xi);
+  // odd log2(N): one radix-2 stage first, then radix-4
+  constexpr bool odd = (N == 2) || (N == 8) || (N == 32);
+  if constexpr (odd) {
+#pragma unroll
+    for (int s = 0; s < N; s += 2) {
+      const T ar = xr[s], ai = xi[s];
+      xr[s] = ar + xr[s + 1]; xi[s] = ai + xi[s + 1];
+      xr[s + 1] = ar - xr[s + 1]; xi[s + 1] = ai - xi[s + 1];
+    }
+    fft_stages<N, SIGN, 2>(xr, xi);
+  } else {
+    fft_stages<N, SIGN, 1>(xr, xi);
+  }
 }
 
 }  // namespace boltz
