@@ -59,35 +59,41 @@ struct CollideArgs {
 
 // Status bits of g_boltz_status.
 constexpr unsigned kStatusNonFinite = 1u;
-constexpr unsigned kStatusTimeout = 2u;
 
 template <typename T, int N, int C>
 struct CollideCfg {
   static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
   static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
-  // padded row of the x-plane buffer: conflict-free row-wise 16-byte accesses (float2
-  // rows padded to a multiple of 16 bytes) and column-wise accesses
-  static constexpr int ROW = sizeof(T) == 4 ? N + 2 : N + 1;
   static constexpr int WARPS = THREADS / 32;
   using T2 = typename Vec2<T>::type;
+  static constexpr bool kF32 = sizeof(T) == 4;
   // float32: the spectrum pencil of each thread stays in registers and the x-plane
   // buffer is double-buffered (one cluster barrier per direction); float64 (register
   // bound) keeps the spectrum in shared memory with a single x-plane buffer.
-  static constexpr bool kRegSpec = sizeof(T) == 4;
+  static constexpr bool kRegSpec = kF32;
   static constexpr int NXB = kRegSpec ? 2 : 1;
+  // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
+  // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
+  // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
+  // kz) then stores 32 contiguous 16-byte chunks to a peer: full 32-byte sectors on the
+  // SM-to-SM network.  RW = N + 1 (odd) keeps the in-plane passes conflict-free with lanes
+  // ordered (x % VEC, ky) and (x % VEC, z).
+  static constexpr int VEC = kF32 ? 2 : 1;
+  static constexpr int NCH = NP / VEC;  // chunks per (ky, k)
+  static constexpr int RW = N + 1;
   static constexpr size_t FH = kRegSpec ? 0 : (size_t)N * NP * N;  // spectrum slab [kx][kyl][kz]
-  static constexpr size_t XB = (size_t)NP * N * ROW;                // x-plane buffer [xl][ky][kz|z]
-  static constexpr size_t TB = (size_t)NP * N * N;                  // table slab [kyl][kx][kz]
-  static constexpr size_t TB_BYTES = TB * sizeof(T2);
+  static constexpr size_t XB = (size_t)NCH * N * RW * VEC;
   static constexpr size_t OFF_XB = FH * sizeof(T2);
-  static constexpr size_t OFF_TB = OFF_XB + NXB * XB * sizeof(T2);
-  static constexpr size_t OFF_RED = OFF_TB + TB_BYTES;
+  static constexpr size_t OFF_RED = OFF_XB + NXB * XB * sizeof(T2);
   // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA
-  static constexpr size_t OFF_MBAR = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
-  static constexpr size_t SMEM = OFF_MBAR + 16;
+  static constexpr size_t SMEM = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
   static_assert(THREADS % 32 == 0, "whole warps");
-  static_assert(OFF_TB % 16 == 0 && TB_BYTES % 16 == 0, "bulk copies need 16-byte alignment");
+  static_assert(NP % VEC == 0, "whole chunks");
+  static_assert(OFF_XB % 16 == 0 && (XB * sizeof(T2)) % 16 == 0, "16-byte aligned buffers");
   static_assert(SMEM <= 232448, "shared memory per CTA");
+  static __device__ __forceinline__ int elem(int xl, int ky, int k) {
+    return ((xl / VEC) * N + ky) * RW * VEC + k * VEC + xl % VEC;
+  }
 };
 
 template <int C>
@@ -124,87 +130,35 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t r) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(r));
   return out;
 }
-__device__ __forceinline__ void st_cluster(uint32_t a, float2 v) {
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(a), "f"(v.x), "f"(v.y) : "memory");
-}
-__device__ __forceinline__ void st_cluster(uint32_t a, double2 v) {
-  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" :: "r"(a), "d"(v.x), "d"(v.y) : "memory");
-}
-__device__ __forceinline__ float2 ld_cluster_f2(uint32_t a) {
-  float2 v;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ double2 ld_cluster_d2(uint32_t a) {
-  double2 v;
-  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
-  return v;
-}
-template <typename T2> __device__ __forceinline__ T2 ld_cluster(uint32_t a);
-template <> __device__ __forceinline__ float2 ld_cluster<float2>(uint32_t a) { return ld_cluster_f2(a); }
-template <> __device__ __forceinline__ double2 ld_cluster<double2>(uint32_t a) { return ld_cluster_d2(a); }
 
-// Row of N complex values: 16-byte vector accesses for float2 (two values per access).
-template <int N>
-__device__ __forceinline__ void load_row(const float2* row, float (&re)[N], float (&im)[N]) {
-  const float4* r4 = reinterpret_cast<const float4*>(row);
-#pragma unroll
-  for (int i = 0; i < N / 2; ++i) {
-    const float4 v = r4[i];
-    re[2 * i] = v.x; im[2 * i] = v.y; re[2 * i + 1] = v.z; im[2 * i + 1] = v.w;
-  }
+// One 16-byte chunk of the x-plane buffer: two float2 (x, x + 1) or one double2.
+__device__ __forceinline__ void st_cluster_chunk(uint32_t a, const float* re, const float* im) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};"
+               :: "r"(a), "f"(re[0]), "f"(im[0]), "f"(re[1]), "f"(im[1]) : "memory");
 }
-template <int N>
-__device__ __forceinline__ void load_row(const double2* row, double (&re)[N], double (&im)[N]) {
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const double2 v = row[i];
-    re[i] = v.x; im[i] = v.y;
-  }
+__device__ __forceinline__ void st_cluster_chunk(uint32_t a, const double* re, const double* im) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" :: "r"(a), "d"(re[0]), "d"(im[0]) : "memory");
 }
-template <int N>
-__device__ __forceinline__ void store_row(float2* row, const float (&re)[N], const float (&im)[N]) {
-  float4* r4 = reinterpret_cast<float4*>(row);
-#pragma unroll
-  for (int i = 0; i < N / 2; ++i) r4[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+__device__ __forceinline__ void ld_cluster_chunk(uint32_t a, float* re, float* im) {
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(re[0]), "=f"(im[0]), "=f"(re[1]), "=f"(im[1]) : "r"(a) : "memory");
 }
-template <int N>
-__device__ __forceinline__ void store_row(double2* row, const double (&re)[N], const double (&im)[N]) {
-#pragma unroll
-  for (int i = 0; i < N; ++i) row[i] = make_double2(re[i], im[i]);
+__device__ __forceinline__ void ld_cluster_chunk(uint32_t a, double* re, double* im) {
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(re[0]), "=d"(im[0]) : "r"(a) : "memory");
 }
-
-// Bulk asynchronous copy of `bytes` (multiple of 16) from global memory into this CTA's
-// shared memory, completing on the mbarrier at `mbar` (expect_tx set by the caller).
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+__device__ __forceinline__ void st_local_chunk(float2* p, const float* re, const float* im) {
+  *reinterpret_cast<float4*>(p) = make_float4(re[0], im[0], re[1], im[1]);
 }
-
-// Thread 0: arm the mbarrier for `bytes` and copy one table slab (chunks of <= 16 KiB).
-__device__ __forceinline__ void load_table_slab(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes)
-               : "memory");
-  const uint32_t chunk = 16384;
-  for (uint32_t off = 0; off < bytes; off += chunk) {
-    const uint32_t nb = (bytes - off < chunk) ? (bytes - off) : chunk;
-    bulk_copy_g2s(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, nb, mbar);
-  }
+__device__ __forceinline__ void st_local_chunk(double2* p, const double* re, const double* im) {
+  *p = make_double2(re[0], im[0]);
 }
-
-// Bounded wait for the phase `parity` of the mbarrier.  Returns false (and flags the
-// device status) if the copy did not complete within the iteration limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    uint32_t done;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
-    if (done) return true;
-  }
-  atomicOr(&g_boltz_status, kStatusTimeout);
-  return false;
+__device__ __forceinline__ void ld_local_chunk(const float2* p, float* re, float* im) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  re[0] = v.x; im[0] = v.y; re[1] = v.z; im[1] = v.w;
+}
+__device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, double* im) {
+  const double2 v = *p;
+  re[0] = v.x; im[0] = v.y;
 }
 
 template <typename T, typename TIO, int N, int C>
@@ -212,48 +166,41 @@ __global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, 1)
 collide_kernel(const CollideArgs args) {
   using Cfg = CollideCfg<T, N, C>;
   using T2 = typename Cfg::T2;
-  constexpr int NP = Cfg::NP, ROW = Cfg::ROW, WARPS = Cfg::WARPS;
+  constexpr int NP = Cfg::NP, WARPS = Cfg::WARPS, VEC = Cfg::VEC, NCH = Cfg::NCH, RW_ = Cfg::RW;
   constexpr int n = N * N * N;
   constexpr bool kRegSpec = Cfg::kRegSpec;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T2* Fh = reinterpret_cast<T2*>(smem_raw);                       // unused when kRegSpec
   T2* XB0 = reinterpret_cast<T2*>(smem_raw + Cfg::OFF_XB);
-  T2* TB = reinterpret_cast<T2*>(smem_raw + Cfg::OFF_TB);
   double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::OFF_MBAR);
 
   const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const long long cell = blockIdx.x / C;
   const int t = threadIdx.x;
-  const int tA = t / N, tB = t % N;
+  // spectral passes: thread (kyl, kz), lanes along kz
+  const int kyl = t / N, kzt = t % N;
+  // physical passes: thread (xl, ky) in the kz pass, (xl, z) in the ky pass / epilogue,
+  // lanes ordered (xl % VEC, ky or z), xl / VEC slowest
+  const int xlt = (t / (VEC * N)) * VEC + t % VEC, grp = (t / VEC) % N;
+  const int zt = grp;
   const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
   const T2* tab = reinterpret_cast<const T2*>(args.tab);
   const int M_eff = args.M_eff;
-  // this CTA's ky-slab of direction j: tab + j n + rank NP N N, contiguous
-  const size_t slab_off = (size_t)rank * NP * N * N;
-
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    load_table_slab(TB, tab + slab_off, (uint32_t)Cfg::TB_BYTES, mbar);  // direction 0
-  }
-  uint32_t phase = 0;
-  bool tb_pending = true;   // a table slab is being copied into TB
-  bool timed_out = false;
+  const int ky_own = rank * NP + kyl;  // spectral ky of this thread's pencils
+  const int x_own = rank * NP + xlt;   // physical x of this thread's rows
 
   T re[N], im[N];
   T fr[kRegSpec ? N : 1], fi[kRegSpec ? N : 1];  // spectrum pencil (kRegSpec)
 
   const double L = args.geom.L, dv = args.geom.dv;
   const int lane = t & 31, warp = t >> 5;
-  // ---- forward transform, pass along y: thread (x = rank NP + tA, z = tB) ----------
+  // ---- forward transform, pass along y: thread (x, z) --------------------------------
   {
-    const int x = rank * NP + tA;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // sum_y f, sum_y y f, sum_y y^2 f (targets)
 #pragma unroll
     for (int y = 0; y < N; ++y) {
-      const TIO fv = fin[(x * N + y) * N + tB];
+      const TIO fv = fin[(x_own * N + y) * N + zt];
       re[y] = (T)fv;
       im[y] = T(0);
       if (args.compute_targets) {
@@ -264,7 +211,7 @@ collide_kernel(const CollideArgs args) {
     }
     if (args.compute_targets) {
       // Phi f over this thread's y-row: v_y = -L + y dv
-      const double vx = -L + x * dv, vz = -L + tB * dv;
+      const double vx = -L + x_own * dv, vz = -L + zt * dv;
       const double sy = -L * s0 + dv * s1;                              // sum v_y f
       const double syy = L * L * s0 - 2.0 * L * dv * s1 + dv * dv * s2;  // sum v_y^2 f
       double m[5] = {s0, vx * s0, sy, vz * s0, 0.5 * ((vx * vx + vz * vz) * s0 + syy)};
@@ -276,7 +223,7 @@ collide_kernel(const CollideArgs args) {
     }
     fft_regs<N, -1>(re, im);
 #pragma unroll
-    for (int k = 0; k < N; ++k) XB0[(tA * N + k) * ROW + tB] = mk2<T>(re[k], im[k]);
+    for (int k = 0; k < N; ++k) XB0[Cfg::elem(xlt, k, zt)] = mk2<T>(re[k], im[k]);
   }
   __syncthreads();
   if (args.compute_targets && t < 5) {
@@ -284,31 +231,37 @@ collide_kernel(const CollideArgs args) {
     for (int w = 0; w < WARPS; ++w) v += red[w * 5 + t];
     red[(WARPS + 1) * 5 + t] = v;  // this CTA's Phi f_in
   }
-  // ---- pass along z: thread (xl = tA, ky = tB) ---------------------------------------
+  // ---- pass along z: thread (xl, ky) ----------------------------------------------------
   {
-    T2* row = XB0 + (tA * N + tB) * ROW;
-    load_row<N>(row, re, im);
+    T2* col = XB0 + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const T2 v = col[z * VEC];
+      re[z] = v.x;
+      im[z] = v.y;
+    }
     fft_regs<N, -1>(re, im);
-    store_row<N>(row, re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) col[k * VEC] = mk2<T>(re[k], im[k]);
   }
   cluster_barrier<C>();
-  // ---- pass along x (remote x-planes): thread (kyl = tA, kz = tB) --------------------
+  // ---- pass along x, gathering the peers' x-planes: thread (kyl, kz) -------------------
   {
-    const int ky = rank * NP + tA;
+    // chunk c of CTA q holds x = q NP + c VEC + (0 .. VEC-1)
 #pragma unroll
-    for (int x = 0; x < N; ++x) {
-      T2 v;
+    for (int c = 0; c < NCH; ++c) {
+      const T2* src = XB0 + Cfg::elem(c * VEC, ky_own, kzt);
       if constexpr (C > 1) {
-        v = ld_cluster<T2>(cluster_addr(smem_u32(XB0 + ((x % NP) * N + ky) * ROW + tB), x / NP));
+        const uint32_t a = smem_u32(src);
+#pragma unroll
+        for (int q = 0; q < C; ++q) ld_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
       } else {
-        v = XB0[(x * N + ky) * ROW + tB];
+        ld_local_chunk(src, re + c * VEC, im + c * VEC);
       }
-      re[x] = v.x;
-      im[x] = v.y;
     }
     fft_regs<N, -1>(re, im);
     const T scale = T(1) / T(n);
-    const bool nyq = (ky == N / 2) || (tB == N / 2);
+    const bool nyq = (ky_own == N / 2) || (kzt == N / 2);
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
       // Every mode with a component -N/2 is removed so each inverse transform is real.
@@ -318,7 +271,7 @@ collide_kernel(const CollideArgs args) {
         fr[kx] = vr;
         fi[kx] = vi;
       } else {
-        Fh[(kx * NP + tA) * N + tB] = mk2<T>(vr, vi);
+        Fh[(kx * NP + kyl) * N + kzt] = mk2<T>(vr, vi);
       }
     }
   }
@@ -331,57 +284,53 @@ collide_kernel(const CollideArgs args) {
   for (int j = 0; j <= M_eff; ++j) {
     T2* XB = XB0 + (kRegSpec ? ((j + 1) & 1) * Cfg::XB : 0);
     const T wj = (j < M_eff) ? (T)args.w[j] : T(0);  // issued early, used after the passes
-    if (tb_pending) {
-      timed_out |= !mbar_wait(mbar, phase);
-      phase ^= 1u;
-      tb_pending = false;
-    }
-    {  // pass along kx with the coefficients: thread (kyl = tA, kz = tB)
-      const int ky = rank * NP + tA;
-      const T2* tj = TB + tA * N * N + tB;
+    {  // pass along kx with the coefficients: thread (kyl, kz); tables straight from L2
+      const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
 #pragma unroll
       for (int kx = 0; kx < N; ++kx) {
         T2 c;
         if constexpr (kRegSpec) {
           c = mk2<T>(fr[kx], fi[kx]);
         } else {
-          c = Fh[(kx * NP + tA) * N + tB];
+          c = Fh[(kx * NP + kyl) * N + kzt];
         }
-        const T2 ab = tj[kx * N];
+        const T2 ab = __ldg(tj + kx * N);
         re[kx] = ab.x * c.x - ab.y * c.y;
         im[kx] = ab.x * c.y + ab.y * c.x;
       }
       fft_regs<N, +1>(re, im);
-      if constexpr (C > 1) {
-        const uint32_t mine = smem_u32(XB + ky * ROW + tB);
+      // outputs x = q NP + c VEC + (0 .. VEC-1) go to chunk c of CTA q at (ky, kz)
 #pragma unroll
-        for (int q = 0; q < C; ++q) {
-          const uint32_t dst = cluster_addr(mine, q);
+      for (int c = 0; c < NCH; ++c) {
+        T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
+        if constexpr (C > 1) {
+          const uint32_t a = smem_u32(dst);
 #pragma unroll
-          for (int xl = 0; xl < NP; ++xl)
-            st_cluster(dst + (uint32_t)(xl * N * ROW * sizeof(T2)), mk2<T>(re[q * NP + xl], im[q * NP + xl]));
+          for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+        } else {
+          st_local_chunk(dst, re + c * VEC, im + c * VEC);
         }
-      } else {
-#pragma unroll
-        for (int x = 0; x < N; ++x) XB[(x * N + ky) * ROW + tB] = mk2<T>(re[x], im[x]);
       }
     }
     cluster_barrier<C>();
-    if (j < M_eff) {  // every thread of this CTA is done with the table slab: fetch the next
-      if (t == 0) load_table_slab(TB, tab + (size_t)(j + 1) * n + slab_off, (uint32_t)Cfg::TB_BYTES, mbar);
-      tb_pending = true;
-    }
-    {  // pass along kz: thread (xl = tA, ky = tB)
-      T2* row = XB + (tA * N + tB) * ROW;
-      load_row<N>(row, re, im);
+    {  // pass along kz: thread (xl, ky)
+      T2* col = XB + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+      for (int kz = 0; kz < N; ++kz) {
+        const T2 v = col[kz * VEC];
+        re[kz] = v.x;
+        im[kz] = v.y;
+      }
       fft_regs<N, +1>(re, im);
-      store_row<N>(row, re, im);
+#pragma unroll
+      for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
     }
     __syncthreads();
-    {  // pass along ky: thread (xl = tA, z = tB); outputs along y
+    {  // pass along ky: thread (xl, z); outputs along y
+      const T2* col = XB + Cfg::elem(xlt, 0, zt);
 #pragma unroll
       for (int ky = 0; ky < N; ++ky) {
-        const T2 v = XB[(tA * N + ky) * ROW + tB];
+        const T2 v = col[ky * (RW_ * VEC)];
         re[ky] = v.x;
         im[ky] = v.y;
       }
@@ -397,15 +346,15 @@ collide_kernel(const CollideArgs args) {
     }
   }
 
-  // ---- Q = Q+ - f L, projection and update (float64) ---------------------------------
-  const int x = rank * NP + tA;
-  const double vx = -L + x * dv, vz = -L + tB * dv;
+  // ---- Q = Q+ - f L, projection and update (float64): thread (x, z) ------------------
+  const int x = x_own, z = zt;
+  const double vx = -L + x * dv, vz = -L + z * dv;
   const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
   double g[N];
   double S0 = 0.0, S1 = 0.0, S2 = 0.0;  // sum_y g, sum_y y g, sum_y y^2 g over this row
 #pragma unroll
   for (int y = 0; y < N; ++y) {
-    const int idx = (x * N + y) * N + tB;
+    const int idx = (x * N + y) * N + z;
     const TIO fv = fin[idx];
     const T q = acc[y] - (T)fv * re[y];  // Q = Q+ - f L (one rounding in T)
     double gv = args.s * (double)q;
@@ -469,11 +418,9 @@ collide_kernel(const CollideArgs args) {
   for (int y = 0; y < N; ++y) {
     const double val = g[y] + (P0 + (double)y * (P1 + (double)y * P2));
     bad |= !isfinite(val);
-    out[(x * N + y) * N + tB] = (TIO)val;
+    out[(x * N + y) * N + z] = (TIO)val;
   }
   if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
-  // A copy can only still be in flight if a wait gave up: wait once more (bounded).
-  if (timed_out) mbar_wait(mbar, phase ^ 1u);
 }
 
 // Plain sums Phi f per cell, scaled: U[c][r] = scale * sum_v phi_r(v) f(v).  One thread
