@@ -44,6 +44,12 @@ WORKLOADS = {
 }
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor), nominal
+# DRAM bytes (read + write) per cell of one collide_kernel launch, from one ncu capture of
+# the current kernels on a smaller batch of the same workload (traffic grows with the
+# number of cells): profiles/collide_fp32_n32_2048cells.md (505.76 MB / 2048 cells) and
+# profiles/collide_fp64_n32_512cells.md (268.27 MB / 512 cells).  Must be re-taken (or set
+# to None) whenever the kernel changes.
+NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": 505.76e6 / 2048, "fp64": 268.27e6 / 512}
 
 
 def algorithmic_flops(N: int, M: int) -> float:
@@ -115,6 +121,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def shard_cells(rank: int, cells_per_rank: int) -> range:
+    """Cells of the global seeded batch owned by `rank` (weak scaling: a fixed number per
+    rank; cells are independent, so no data is exchanged between ranks)."""
+    return range(rank * cells_per_rank, (rank + 1) * cells_per_rank)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank scalar over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096):
@@ -195,8 +219,8 @@ def run_ours(args, wl):
     chunk = 1024
     for c0 in range(0, cells, chunk):
         c1 = min(cells, c0 + chunk)
-        host[c0:c1] = torch.from_numpy(W.two_maxwellians(cells * ws, N, L, wl["seed"],
-                                                         cells=range(rank * cells + c0, rank * cells + c1)))
+        mine = shard_cells(rank, cells)
+        host[c0:c1] = torch.from_numpy(W.two_maxwellians(cells * ws, N, L, wl["seed"], cells=mine[c0:c1]))
     f0 = host.cuda()
     f = f0.clone()
     stream = torch.cuda.current_stream()
@@ -232,11 +256,7 @@ def run_ours(args, wl):
     B.boltz_stream_status(stream)
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = tt.item()
+    total_ms = max_over_ranks(total_ms, "cuda")
     value = cells * ws * args.steps / (total_ms / 1000.0)
 
     # drift of the conserved moments over the timed steps, on the stored state
@@ -262,11 +282,7 @@ def run_ours(args, wl):
     barrier()
     B.boltz_stream_status(stream)
     e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = tt.item()
+    e2e_ms = max_over_ranks(e2e_ms, "cuda")
     e2e_value = cells * ws * e2e_steps / (e2e_ms / 1000.0)
     nbytes = host.numel() * host.element_size()
 
@@ -299,7 +315,10 @@ def run_ours(args, wl):
             "dtype": "f64" if wl["prec"] == "fp64" else "f32", "data": "synthetic",
             "config": config_of(args, wl),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (NCU_DRAM_BYTES_PER_CELL.get(wl["prec"]) or 0) * cells or None,
+                         "traffic_unit": "bytes per launch (ncu dram read+write, scaled by cells)",
+                         "algorithmic_bytes": 2 * N ** 3 * (8 if wl["f64"] else 4) * cells,
                          "kernel": "collide_kernel (one launch per step)",
                          "flops_per_cell": flops_cell, "peak_source": peak_note},
             "e2e": {"value": e2e_value, "unit": "cell-collisions/s", "h2d_bytes_per_step": nbytes,

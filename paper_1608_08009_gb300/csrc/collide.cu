@@ -281,67 +281,91 @@ collide_kernel(const CollideArgs args) {
   T acc[N];
 #pragma unroll
   for (int y = 0; y < N; ++y) acc[y] = T(0);
-  for (int j = 0; j <= M_eff; ++j) {
-    T2* XB = XB0 + (kRegSpec ? ((j + 1) & 1) * Cfg::XB : 0);
-    const T wj = (j < M_eff) ? (T)args.w[j] : T(0);  // issued early, used after the passes
-    {  // pass along kx with the coefficients: thread (kyl, kz); tables straight from L2
-      const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
+
+  // pass along kx with the coefficients of term j: thread (kyl, kz), tables from L2;
+  // outputs x = q NP + c VEC + (0 .. VEC-1) go to chunk c of CTA q at (ky, kz)
+  auto pass_kx = [&](int j, T2* XB) {
+    const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
 #pragma unroll
-      for (int kx = 0; kx < N; ++kx) {
-        T2 c;
-        if constexpr (kRegSpec) {
-          c = mk2<T>(fr[kx], fi[kx]);
-        } else {
-          c = Fh[(kx * NP + kyl) * N + kzt];
-        }
-        const T2 ab = __ldg(tj + kx * N);
-        re[kx] = ab.x * c.x - ab.y * c.y;
-        im[kx] = ab.x * c.y + ab.y * c.x;
+    for (int kx = 0; kx < N; ++kx) {
+      T2 c;
+      if constexpr (kRegSpec) {
+        c = mk2<T>(fr[kx], fi[kx]);
+      } else {
+        c = Fh[(kx * NP + kyl) * N + kzt];
       }
-      fft_regs<N, +1>(re, im);
-      // outputs x = q NP + c VEC + (0 .. VEC-1) go to chunk c of CTA q at (ky, kz)
+      const T2 ab = __ldg(tj + kx * N);
+      re[kx] = ab.x * c.x - ab.y * c.y;
+      im[kx] = ab.x * c.y + ab.y * c.x;
+    }
+    fft_regs<N, +1>(re, im);
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
-        if constexpr (C > 1) {
-          const uint32_t a = smem_u32(dst);
+    for (int c = 0; c < NCH; ++c) {
+      T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
+      if constexpr (C > 1) {
+        const uint32_t a = smem_u32(dst);
 #pragma unroll
-          for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
-        } else {
-          st_local_chunk(dst, re + c * VEC, im + c * VEC);
-        }
+        for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+      } else {
+        st_local_chunk(dst, re + c * VEC, im + c * VEC);
       }
     }
-    cluster_barrier<C>();
-    {  // pass along kz: thread (xl, ky)
-      T2* col = XB + Cfg::elem(xlt, grp, 0);
+  };
+  // pass along kz: thread (xl, ky)
+  auto pass_kz = [&](T2* XB) {
+    T2* col = XB + Cfg::elem(xlt, grp, 0);
 #pragma unroll
-      for (int kz = 0; kz < N; ++kz) {
-        const T2 v = col[kz * VEC];
-        re[kz] = v.x;
-        im[kz] = v.y;
-      }
-      fft_regs<N, +1>(re, im);
-#pragma unroll
-      for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
+    for (int kz = 0; kz < N; ++kz) {
+      const T2 v = col[kz * VEC];
+      re[kz] = v.x;
+      im[kz] = v.y;
     }
-    __syncthreads();
-    {  // pass along ky: thread (xl, z); outputs along y
-      const T2* col = XB + Cfg::elem(xlt, 0, zt);
+    fft_regs<N, +1>(re, im);
 #pragma unroll
-      for (int ky = 0; ky < N; ++ky) {
-        const T2 v = col[ky * (RW_ * VEC)];
-        re[ky] = v.x;
-        im[ky] = v.y;
-      }
-      fft_regs<N, +1>(re, im);
-      if (j < M_eff) {
+    for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
+  };
+  // pass along ky: thread (xl, z); outputs along y.  accumulate: Q+ += w Re Im; otherwise
+  // re[] keeps the loss multiplier L(v) along y.
+  auto pass_ky = [&](const T2* XB, T wj, bool accumulate) {
+    const T2* col = XB + Cfg::elem(xlt, 0, zt);
 #pragma unroll
-        for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
-      }
-      // for j == M_eff, re[] now holds the loss multiplier L(v) along y
+    for (int ky = 0; ky < N; ++ky) {
+      const T2 v = col[ky * (RW_ * VEC)];
+      re[ky] = v.x;
+      im[ky] = v.y;
     }
-    if constexpr (!kRegSpec) {
+    fft_regs<N, +1>(re, im);
+    if (accumulate) {
+#pragma unroll
+      for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
+    }
+  };
+
+  if constexpr (kRegSpec) {
+    // Two x-plane buffers; term j uses buffer (j + 1) % 2.  The ky pass of term j - 1
+    // runs between the scatter of term j and the cluster barrier, so the remote stores
+    // drain behind it.  It reads the other buffer, and every CTA finishes it before
+    // arriving, so no peer scatters term j + 1 into that buffer while it is read.
+    T w_prev = T(0);
+    for (int j = 0; j <= M_eff; ++j) {
+      T2* XBj = XB0 + ((j + 1) & 1) * Cfg::XB;
+      const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+      pass_kx(j, XBj);
+      if (j > 0) pass_ky(XB0 + (j & 1) * Cfg::XB, w_prev, true);
+      cluster_barrier<C>();
+      pass_kz(XBj);
+      __syncthreads();
+      w_prev = wj;
+    }
+    pass_ky(XB0 + ((M_eff + 1) & 1) * Cfg::XB, T(0), false);  // loss term
+  } else {
+    for (int j = 0; j <= M_eff; ++j) {
+      const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+      pass_kx(j, XB0);
+      cluster_barrier<C>();
+      pass_kz(XB0);
+      __syncthreads();
+      pass_ky(XB0, wj, j < M_eff);
       if (j < M_eff) cluster_barrier<C>();  // single buffer: owners done before the next scatter
     }
   }
