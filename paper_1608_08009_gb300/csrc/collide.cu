@@ -10,15 +10,15 @@
 // written once per cell.
 //
 // Work decomposition.  A cell is owned by a thread-block cluster of C CTAs.
-//  * Spectrum: CTA c keeps fhat(kx, ky, kz) for the ky-slab [c N/C, (c+1) N/C) in shared
-//    memory, all kx and kz.
+//  * Spectrum: CTA c keeps fhat(kx, ky, kz) for the ky-slab [c N/C, (c+1) N/C), all kx
+//    and kz: in registers (float32, thread (ky, kz) holds its kx pencil) or shared memory.
 //  * Physical space: CTA q owns the x-slab [q N/C, (q+1) N/C); the gain accumulator of
 //    its points lives in registers (thread (x, z) holds the N values along y).
 //  * One inverse 3D transform = pass along kx (pencils of the CTA's ky-slab, in
 //    registers) whose N outputs are scattered by x into the owners' shared memory through
 //    distributed shared memory, a cluster barrier, then the passes along kz and ky inside
 //    each x-plane of the owner.
-//  * Every 1D pass is a fully unrolled radix-2 FFT of one pencil held by one thread.
+//  * Every 1D pass is a fully unrolled radix-4/2 FFT of one pencil held by one thread.
 // Twiddles, kernel tables and weights are float32 for the BOLTZ_FP32_FFT path and
 // float64 for BOLTZ_FP64.  Moments, projection and the update are float64 in both.
 #include <cooperative_groups.h>
