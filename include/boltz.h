@@ -99,7 +99,8 @@ void boltz_default_opts(boltz_grid_opts* opts);
  * separable in 3D and a rank-r radial expansion is tabulated instead (r terms per
  * direction).  Builds the tables on the host in float64 and copies them to the
  * current device.
- *   N_v     points per axis; supported: 16, 32.
+ *   N_v     points per axis; supported: 8, 16, 24, 32 (48 and 64 return
+ *           BOLTZ_EUNSUPPORTED: their register pencils do not fit this kernel design).
  *   L       half-width of the velocity box [-L, L)^3, > 0.
  *   gamma   VHS exponent in [-3, 1] (1 = hard spheres, 0 = Maxwell molecules).
  *   M_dirs  number of directions, 1..4096.

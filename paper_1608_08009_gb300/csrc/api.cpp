@@ -80,8 +80,8 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
     set_error("null output handle");
     return BOLTZ_EINVAL;
   }
-  if (N_v != 16 && N_v != 32) {
-    set_error("N_v must be 16 or 32 in this build");
+  if (N_v != 8 && N_v != 16 && N_v != 24 && N_v != 32) {
+    set_error("N_v must be 8, 16, 24 or 32 in this build");
     return (N_v > 0 && N_v % 2 == 0) ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
   }
   if (!(L > 0) || !std::isfinite(L)) {

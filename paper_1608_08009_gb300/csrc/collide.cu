@@ -502,11 +502,11 @@ static boltz_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 boltz_status upload_tables(boltz_grid_s* g) {
-  // twiddles exp(2 pi i m / 64), host libm in float64
-  double tc[64], ts[64];
-  float fc[64], fs[64];
-  for (int m = 0; m < 64; ++m) {
-    const double ang = 2.0 * 3.14159265358979323846 * m / 64.0;
+  // twiddles exp(2 pi i m / kTw), host libm in float64
+  double tc[kTw], ts[kTw];
+  float fc[kTw], fs[kTw];
+  for (int m = 0; m < kTw; ++m) {
+    const double ang = 2.0 * 3.14159265358979323846 * m / (double)kTw;
     tc[m] = std::cos(ang);
     ts[m] = std::sin(ang);
     fc[m] = (float)tc[m];
@@ -591,13 +591,16 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
 }
 
 bool collide_supported(int N, int prec) {
-  return (N == 16 || N == 32) && (prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT);
+  return (N == 8 || N == 16 || N == 24 || N == 32) && (prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT);
 }
 
 template <typename T, typename TIO>
 static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  // cluster sizes: the smallest C whose per-CTA slab fits shared memory and registers
   constexpr bool dbl = sizeof(T) == 8;
+  if (g->N == 8) return launch_impl<T, TIO, 8, 1>(a, n_cells, st);
   if (g->N == 16) return launch_impl<T, TIO, 16, dbl ? 2 : 1>(a, n_cells, st);
+  if (g->N == 24) return launch_impl<T, TIO, 24, dbl ? 3 : 2>(a, n_cells, st);
   if (g->N == 32) return launch_impl<T, TIO, 32, dbl ? 8 : 4>(a, n_cells, st);
   set_error("no collision kernel for this N");
   return BOLTZ_EUNSUPPORTED;

@@ -1,21 +1,25 @@
-// In-register radix-2 FFT of one pencil, fully unrolled (N = 16, 32, 64).
+// In-register FFT of one pencil, fully unrolled: N = 2^k (radix-4/2) or N = 3 * 2^k
+// (one radix-3 decimation over three power-of-two sub-transforms), N <= 64.
 //
 // Used for every 1D pass of the 3D transforms of the fast spectral collision operator
 // (arxiv 1608.08009, Sec. 3.3, Eqs. FU/FC; Sec. 4.2: one forward transform of f and, per
 // direction, the inverse transforms that dominate the cost).  The twiddles
-// exp(2 pi i m / 64) come from constant memory, filled once per device by the host with
-// the host libm cos/sin in float64 (and rounded to float32 for the float32 path).
+// exp(2 pi i m / 192) (192 = lcm of every stage length used) come from constant memory,
+// filled once per device by the host with the host libm cos/sin in float64 (and rounded
+// to float32 for the float32 path).
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace boltz {
 
+constexpr int kTw = 192;
+
 // Defined here; this header is included by exactly one translation unit (collide.cu).
-__constant__ double c_twc64[64];
-__constant__ double c_tws64[64];
-__constant__ float c_twc32[64];
-__constant__ float c_tws32[64];
+__constant__ double c_twc64[kTw];
+__constant__ double c_tws64[kTw];
+__constant__ float c_twc32[kTw];
+__constant__ float c_tws32[kTw];
 
 template <typename T> __device__ __forceinline__ T tw_cos(int m);
 template <typename T> __device__ __forceinline__ T tw_sin(int m);
@@ -42,18 +46,19 @@ struct BitReverse {
   }
 };
 
-// Complex multiply of (br, bi) by the twiddle exp(SIGN 2 pi i m / 64), m a compile-time
-// constant after unrolling (m = 0 and m = 16 need no multiplication).
+// Complex multiply of (br, bi) by the twiddle exp(SIGN 2 pi i m / 192), m a compile-time
+// constant after unrolling (multiples of a quarter turn need no multiplication).
 template <int SIGN, typename T>
 __device__ __forceinline__ void twiddle(int m, T br, T bi, T& tr, T& ti) {
+  m %= kTw;
   if (m == 0) {
     tr = br; ti = bi;
-  } else if (m == 16) {  // exp(SIGN i pi / 2) = SIGN i
+  } else if (m == kTw / 4) {  // SIGN i
     tr = (SIGN > 0) ? -bi : bi;
     ti = (SIGN > 0) ? br : -br;
-  } else if (m == 32) {  // -1
+  } else if (m == kTw / 2) {  // -1
     tr = -br; ti = -bi;
-  } else if (m == 48) {  // -SIGN i
+  } else if (m == 3 * kTw / 4) {  // -SIGN i
     tr = (SIGN > 0) ? bi : -bi;
     ti = (SIGN > 0) ? -br : br;
   } else {
@@ -74,7 +79,7 @@ __device__ __forceinline__ void fft_stages(T (&xr)[N], T (&xi)[N]) {
   if constexpr (SPAN < N) {
     if constexpr (4 * SPAN <= N) {
       constexpr int L = 4 * SPAN;
-      constexpr int stride = 64 / L;  // exp(SIGN 2 pi i k / L) = twiddle index k * stride
+      constexpr int stride = kTw / L;  // exp(SIGN 2 pi i k / L) = twiddle index k * stride
 #pragma unroll
       for (int s = 0; s < N; s += L) {
 #pragma unroll
@@ -100,7 +105,7 @@ __device__ __forceinline__ void fft_stages(T (&xr)[N], T (&xi)[N]) {
       fft_stages<N, SIGN, 4 * SPAN>(xr, xi);
     } else {
       constexpr int L = 2 * SPAN;
-      constexpr int stride = 64 / L;
+      constexpr int stride = kTw / L;
 #pragma unroll
       for (int s = 0; s < N; s += L) {
 #pragma unroll
@@ -118,31 +123,77 @@ __device__ __forceinline__ void fft_stages(T (&xr)[N], T (&xi)[N]) {
   }
 }
 
-// x_k <- sum_j x_j exp(SIGN 2 pi i j k / N); no scaling.  SIGN = -1 forward, +1 inverse.
+// Power-of-two transform: bit reversal (register renaming), one radix-2 stage when
+// log2 N is odd, then radix-4 stages.
 template <int N, int SIGN, typename T>
-__device__ __forceinline__ void fft_regs(T (&xr)[N], T (&xi)[N]) {
-  static_assert((N & (N - 1)) == 0 && N >= 2 && N <= 64, "power of two up to 64");
-  constexpr BitReverse<N> rev{};
+__device__ __forceinline__ void fft_pow2(T (&xr)[N], T (&xi)[N]) {
+  static_assert((N & (N - 1)) == 0 && N >= 1 && N <= 64, "power of two up to 64");
+  if constexpr (N == 1) {
+    return;
+  } else {
+    constexpr BitReverse<N> rev{};
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int j = rev.v[i];
-    if (j > i) {
-      T t = xr[i]; xr[i] = xr[j]; xr[j] = t;
-      t = xi[i]; xi[i] = xi[j]; xi[j] = t;
+    for (int i = 0; i < N; ++i) {
+      const int j = rev.v[i];
+      if (j > i) {
+        T t = xr[i]; xr[i] = xr[j]; xr[j] = t;
+        t = xi[i]; xi[i] = xi[j]; xi[j] = t;
+      }
+    }
+    constexpr bool odd = (N == 2) || (N == 8) || (N == 32);
+    if constexpr (odd) {
+#pragma unroll
+      for (int s = 0; s < N; s += 2) {
+        const T ar = xr[s], ai = xi[s];
+        xr[s] = ar + xr[s + 1]; xi[s] = ai + xi[s + 1];
+        xr[s + 1] = ar - xr[s + 1]; xi[s + 1] = ai - xi[s + 1];
+      }
+      fft_stages<N, SIGN, 2>(xr, xi);
+    } else {
+      fft_stages<N, SIGN, 1>(xr, xi);
     }
   }
-  // odd log2(N): one radix-2 stage first, then radix-4
-  constexpr bool odd = (N == 2) || (N == 8) || (N == 32);
-  if constexpr (odd) {
-#pragma unroll
-    for (int s = 0; s < N; s += 2) {
-      const T ar = xr[s], ai = xi[s];
-      xr[s] = ar + xr[s + 1]; xi[s] = ai + xi[s + 1];
-      xr[s + 1] = ar - xr[s + 1]; xi[s + 1] = ai - xi[s + 1];
-    }
-    fft_stages<N, SIGN, 2>(xr, xi);
+}
+
+// x_k <- sum_j x_j exp(SIGN 2 pi i j k / N); no scaling.  SIGN = -1 forward, +1 inverse.
+// N = 3 P (P a power of two): a_r[m] = x[3m + r] are transformed with length P, then
+// X[k + qP] = sum_r w3^{rq} W_N^{rk} A_r[k], w3 = exp(SIGN 2 pi i / 3).
+template <int N, int SIGN, typename T>
+__device__ __forceinline__ void fft_regs(T (&xr)[N], T (&xi)[N]) {
+  if constexpr ((N & (N - 1)) == 0) {
+    fft_pow2<N, SIGN>(xr, xi);
   } else {
-    fft_stages<N, SIGN, 1>(xr, xi);
+    static_assert(N % 3 == 0 && ((N / 3) & (N / 3 - 1)) == 0 && N <= 48, "N = 3 * 2^k");
+    constexpr int P = N / 3;
+    T ar[3][P], ai[3][P];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        ar[r][m] = xr[3 * m + r];
+        ai[r][m] = xi[3 * m + r];
+      }
+      fft_pow2<P, SIGN>(ar[r], ai[r]);
+    }
+    const T c3 = T(-0.5);  // cos(2 pi / 3)
+    const T s3 = (SIGN > 0 ? T(1) : T(-1)) * tw_sin<T>(kTw / 3);  // SIGN sin(2 pi / 3)
+    constexpr int stride = kTw / N;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      T b1r, b1i, b2r, b2i;
+      twiddle<SIGN>(k * stride, ar[1][k], ai[1][k], b1r, b1i);
+      twiddle<SIGN>(2 * k * stride, ar[2][k], ai[2][k], b2r, b2i);
+      const T sr = b1r + b2r, si = b1i + b2i;  // b1 + b2
+      const T dr = b1r - b2r, di = b1i - b2i;  // b1 - b2
+      const T mr = ar[0][k] + c3 * sr, mi = ai[0][k] + c3 * si;
+      // w3 b1 + w3^2 b2 = c3 (b1 + b2) + i s3 (b1 - b2), and its conjugate-rotation pair
+      xr[k] = ar[0][k] + sr;
+      xi[k] = ai[0][k] + si;
+      xr[k + P] = mr - s3 * di;
+      xi[k + P] = mi + s3 * dr;
+      xr[k + 2 * P] = mr + s3 * di;
+      xi[k + 2 * P] = mi - s3 * dr;
+    }
   }
 }
 

@@ -66,7 +66,7 @@ def run_collide(grid, f_np, prec, fp64=True, stream=None):
     return Q.double().cpu().numpy()
 
 
-@pytest.mark.parametrize("N,L,M,kind", [(16, 6.0, 32, 0), (32, 8.0, 64, 0), (32, 8.0, 36, 2), (16, 5.0, 20, 1)])
+@pytest.mark.parametrize("N,L,M,kind", [(16, 6.0, 32, 0), (32, 8.0, 64, 0), (32, 8.0, 36, 2), (16, 5.0, 20, 1), (24, 7.0, 20, 1), (8, 4.0, 8, 2)])
 def test_tables_match_oracle(N, L, M, kind):
     with B.Grid(N, L, 1.0, M, dirs_kind=kind) as g:
         e, w, al, ap, D = g.tables()
@@ -79,7 +79,7 @@ def test_tables_match_oracle(N, L, M, kind):
 
 
 @pytest.mark.parametrize("prec", [B.BOLTZ_FP64, B.BOLTZ_FP32_FFT])
-@pytest.mark.parametrize("N,L,M,cells", [(16, 6.0, 32, 5), (32, 8.0, 64, 3)])
+@pytest.mark.parametrize("N,L,M,cells", [(8, 4.0, 16, 7), (16, 6.0, 32, 5), (24, 7.0, 36, 3), (32, 8.0, 64, 3)])
 def test_collide_parity(prec, N, L, M, cells):
     f = W.two_maxwellians(cells, N, L, seed=20161 + N)
     og = oracle_grid(N, L, M)
@@ -151,9 +151,10 @@ def test_projected_Q_has_zero_moments():
             assert (U.abs() / UA[:, :1]).max().item() < 1e-13
 
 
+@pytest.mark.parametrize("N,L", [(16, 6.0), (24, 7.0)])
 @pytest.mark.parametrize("rk", [1, 2])
-def test_relax_parity(rk):
-    N, L, M = 16, 6.0, 16
+def test_relax_parity(rk, N, L):
+    M = 16
     f = W.two_maxwellians(3, N, L, seed=44)
     og = oracle_grid(N, L, M)
     ref = O.relax(f, og, 0.004, 3, rk_order=rk)
