@@ -10,7 +10,7 @@ Metric: cell-collisions per second.
 
 Workloads (synthetic, seeded two-Maxwellian cells; no dataset is involved):
   mixed32  -- 32768 cells x 32^3, VHS gamma = 1, M = 64 (8 x 8 product grid), L = 8,
-              dt = 0.005, f stored float32, transforms float32, moments / projection /
+              dt = 0.0025, f stored float32, transforms float32, moments / projection /
               update float64.  Default.
   fp64_32  -- 4096 cells x 32^3, same physics, float64 everywhere (the plain form).
 
@@ -38,9 +38,13 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+# dt: forward Euler is stable while dt * max_v L(v) < 2; the densest cells of these inputs
+# (rho = 4, T = 0.5) reach max L ~ 500 on [-8, 8)^3 and ~ 350 on [-6, 6)^3 (the loss
+# rate grows with the truncation radius R = 4L / (3 + sqrt 2)), so dt = 0.0025 keeps
+# dt * max L <= 1.25 for any number of steps.
 WORKLOADS = {
-    "mixed32": dict(cells=32768, N=32, L=8.0, M=64, gamma=1.0, dt=0.005, prec="fp32_fft", f64=False, seed=20163),
-    "fp64_32": dict(cells=4096, N=32, L=8.0, M=64, gamma=1.0, dt=0.005, prec="fp64", f64=True, seed=20162),
+    "mixed32": dict(cells=32768, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20163),
+    "fp64_32": dict(cells=4096, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp64", f64=True, seed=20162),
 }
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor), nominal
@@ -160,6 +164,96 @@ def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096):
             break
     el = time.perf_counter() - t0
     return U_done / el, U_done, el
+
+
+def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_bytes: int = 2 << 30,
+                max_in_flight: int = 4) -> dict:
+    """Serving load (continuous batching through boltz_server_*): Poisson arrivals at
+    `rate` req/s for `seconds`; each request is one cell relaxing for U{10..200} forward
+    Euler steps, N in {16 (60 %), 32 (35 %), 64 (5 %)}, gamma = 1, M = 64, dt = 0.0025,
+    float32 path, admission by an HBM budget.  64^3 requests are rejected (no kernel for
+    that size in this build).  Latency = completion seen by the host - arrival."""
+    import torch
+
+    from paper_1608_08009_gb300 import boltz as B
+    from paper_1608_08009_gb300 import workloads as W
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_req = int(rng.poisson(rate * seconds))
+    arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
+    sizes = rng.choice([16, 32, 64], size=n_req, p=[0.60, 0.35, 0.05])
+    steps = rng.integers(10, 201, size=n_req)
+    # 16^3 jobs on [-6, 6)^3 (dv = 0.75), 32^3 jobs on [-8, 8)^3 (dv = 0.5)
+    Ls = {16: 6.0, 32: 8.0}
+    grids = {N: B.Grid(N, Ls[N], 1.0, 64) for N in (16, 32)}
+    gidx = {16: 0, 32: 1}
+    stream = torch.cuda.current_stream()
+    server = B.Server([grids[16], grids[32]], B.BOLTZ_FP32_FFT, 0.0025, budget_bytes, stream)
+    reqs = []
+    for k in range(n_req):
+        N = int(sizes[k])
+        if N not in grids:
+            reqs.append(None)
+            continue
+        f = W.two_maxwellians(n_req, N, Ls[N], seed, cells=[k])[0].astype(np.float32).ravel()
+        reqs.append((torch.from_numpy(f).pin_memory(), torch.empty(f.size, dtype=torch.float32).pin_memory()))
+    # warm-up of both grids outside the measured window
+    for N in (16, 32):
+        f = torch.zeros(N ** 3, dtype=torch.float32).pin_memory() + 1e-3
+        o = torch.empty_like(f)
+        j = server.submit(gidx[N], f, o, 2)
+        while not server.poll(j):
+            server.step()
+    torch.cuda.synchronize()
+    done_t = [None] * n_req
+    ids = [None] * n_req
+    nxt, inflight, n_steps, max_res, max_q = 0, [], 0, 0, 0
+    t0 = time.perf_counter()
+    pending = set()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            if reqs[nxt] is not None:
+                ids[nxt] = server.submit(gidx[int(sizes[nxt])], reqs[nxt][0], reqs[nxt][1], int(steps[nxt]))
+                pending.add(nxt)
+            nxt += 1
+        res, q = server.step()
+        n_steps += 1
+        max_res, max_q = max(max_res, res), max(max_q, q)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        inflight.append(ev)
+        if len(inflight) > max_in_flight:
+            inflight.pop(0).synchronize()
+        now = time.perf_counter() - t0
+        for k in list(pending):
+            if server.poll(ids[k]):
+                done_t[k] = now
+                pending.discard(k)
+        if nxt >= n_req and not pending:
+            break
+        if res == 0 and q == 0 and not pending and nxt < n_req:
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+        if now > seconds + 120.0:
+            break
+    wall = time.perf_counter() - t0
+    B.boltz_stream_status(stream)
+    lat = np.array([done_t[k] - arrivals[k] for k in range(n_req) if done_t[k] is not None])
+    served = [k for k in range(n_req) if done_t[k] is not None]
+    cell_steps = int(sum(int(steps[k]) for k in served))
+    server.close()
+    for g in grids.values():
+        g.close()
+    return {"p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "mean_latency_s": float(lat.mean()) if lat.size else None,
+            "completed": len(served), "rejected_64cubed": int(np.sum(sizes == 64)),
+            "unfinished": int(sum(1 for k in range(n_req) if reqs[k] is not None and done_t[k] is None)),
+            "offered_req_per_s": rate, "arrival_window_s": seconds, "wall_s": wall,
+            "cell_collisions_per_s": cell_steps / wall, "server_iterations": n_steps,
+            "max_resident": max_res, "max_queued": max_q, "hbm_budget_bytes": budget_bytes,
+            "mix": "N=16 (L=6): 60 %, N=32 (L=8): 35 %, N=64: 5 % (rejected); steps U{10..200}; M=64; "
+                   "gamma=1; dt=0.0025; f32"}
 
 
 def run_reference(args, wl):
@@ -329,6 +423,8 @@ def run_ours(args, wl):
             "moment_drift_rel": drift,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }
+        if args.serve_seconds > 0 and ws == 1:
+            line["serve"] = run_serving(args.serve_seconds)
         if not args.no_cpu_baseline and ws == 1:
             r, ncell, el = cpu_oracle_rate(wl, budget_s=args.cpu_budget)
             line["cpu_baseline"] = {"value": r, "unit": "cell-collisions/s", "cores": 1, "kind": "oracle",
@@ -353,6 +449,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the float64 comparison of the batch")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving-load window (0: skip)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.cells > 0:

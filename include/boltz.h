@@ -24,7 +24,8 @@
  *  Streams.    `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *              stream).  Every compute call is asynchronous on that stream.
  *  Errors.     Argument errors are returned synchronously and leave the stream
- *              untouched.  Conditions found on the device (non-finite results) are
+ *              untouched.  Conditions found on the device (non-finite results, cell
+ *              indices outside their pool) are
  *              OR-ed into a device status word that boltz_stream_status() reads.  No call
  *              aborts, traps or waits without bound.  boltz_last_error() gives a
  *              thread-local message for the last failing call of the calling thread.
@@ -34,6 +35,7 @@
 #ifndef BOLTZ_H
 #define BOLTZ_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -145,6 +147,44 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
  * f: device array of n_cells * N^3 elements, updated in place.  Errors: EINVAL,
  * EUNSUPPORTED, ECUDA. */
 boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, double dt, int steps, void* stream);
+
+/* Cells addressed through an index array (ragged batches, resident pools): cell c of the
+ * call is slot cell_idx[c] of f (and of Q), with slot s at offset s * N^3.  cell_idx is a
+ * device array of n_cells int64 values; slots must be distinct and lie in
+ * [0, pool_cells).  An index outside the pool is not dereferenced: that cell writes
+ * nothing and boltz_stream_status() later returns BOLTZ_EINVAL.
+ * boltz_collide_indexed: Q(f) of the listed slots (as boltz_collide).
+ * boltz_relax_indexed:   forward-Euler steps of the listed slots in place (as
+ *   boltz_relax with rk_order 1; targets per slot in library scratch sized for the pool).
+ * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+boltz_status boltz_collide_indexed(const boltz_batch* b, const void* f, void* Q, const int64_t* cell_idx,
+                                   int64_t pool_cells, void* stream);
+boltz_status boltz_relax_indexed(const boltz_batch* b, void* f, const int64_t* cell_idx, int64_t pool_cells,
+                                 double dt, int steps, void* stream);
+
+/* ---- Serving: continuous batching of relaxation jobs ------------------------------------
+ * A job is one cell relaxing under df/dt = Q(f) (Sec. 3.1, Eq. relax) for `steps` forward
+ * Euler steps of size dt with the projection after each step (each step projects onto
+ * the moments the cell has at that step).  The server keeps admitted jobs resident in
+ * per-grid device pools of float32 slots, admits queued jobs in arrival order while a
+ * slot and the HBM budget (bytes of resident f over all grids) allow, advances all
+ * resident jobs of a grid by one indexed launch per boltz_server_step, and copies each
+ * finished job back to its host buffer asynchronously.  A job's result does not depend
+ * on which other jobs are resident.  All work runs on `stream`; calls are not thread-safe.
+ *   create: grids (one per grid shape a job may use, kept alive by the caller), prec,
+ *           dt, budget.  Allocates one pool of budget bytes per grid.
+ *   submit: f_host, out_host: N^3 floats each (pinned memory recommended), owned by the
+ *           caller until poll reports the job done; returns a job id.
+ *   step:   admission, one step of every resident job, retirement; reports counts.
+ *   poll:   done = 1 once out_host holds the result. */
+typedef struct boltz_server_s* boltz_server;
+boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec, double dt,
+                                 size_t hbm_budget_bytes, void* stream, boltz_server* out);
+boltz_status boltz_server_submit(boltz_server s, int grid_index, const float* f_host, float* out_host,
+                                 int steps, int64_t* job_id);
+boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued);
+boltz_status boltz_server_poll(boltz_server s, int64_t job_id, int* done);
+boltz_status boltz_server_destroy(boltz_server s);
 
 /* U[c] = (rho, rho u, E) of every cell (Eq. i5 on the grid, Eq. DM), float64,
  * U a device array of n_cells * 5 doubles.  Errors: EINVAL, ECUDA. */

@@ -33,7 +33,9 @@ _STATUS_NAMES = {0: "BOLTZ_OK", 1: "BOLTZ_EINVAL", 2: "BOLTZ_ENOMEM", 3: "BOLTZ_
 
 EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "boltz_collide",
             "boltz_relax", "boltz_moments", "boltz_stream_status", "boltz_last_error",
-            "boltz_grid_info", "boltz_grid_tables", "boltz_version", "boltz_relax_noalloc")
+            "boltz_grid_info", "boltz_grid_tables", "boltz_version", "boltz_relax_noalloc",
+            "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
+            "boltz_server_step", "boltz_server_poll", "boltz_server_destroy")
 
 
 class BoltzError(RuntimeError):
@@ -73,6 +75,13 @@ def lib() -> ctypes.CDLL:
         L.boltz_relax.argtypes = [P(boltz_batch), vp, f64, i32, i32, vp]
         L.boltz_moments.argtypes = [P(boltz_batch), vp, vp, vp]
         L.boltz_relax_noalloc.argtypes = [P(boltz_batch), vp, f64, i32, vp]
+        L.boltz_collide_indexed.argtypes = [P(boltz_batch), vp, vp, vp, i64, vp]
+        L.boltz_relax_indexed.argtypes = [P(boltz_batch), vp, vp, i64, f64, i32, vp]
+        L.boltz_server_create.argtypes = [P(vp), i32, i32, f64, ctypes.c_size_t, vp, P(vp)]
+        L.boltz_server_submit.argtypes = [vp, i32, vp, vp, i32, P(i64)]
+        L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
+        L.boltz_server_poll.argtypes = [vp, i64, P(i32)]
+        L.boltz_server_destroy.argtypes = [vp]
         L.boltz_stream_status.argtypes = [vp]
         L.boltz_last_error.argtypes = []
         L.boltz_last_error.restype = ctypes.c_char_p
@@ -82,7 +91,9 @@ def lib() -> ctypes.CDLL:
         L.boltz_version.restype = ctypes.c_char_p
         for name in ("boltz_create_grid", "boltz_destroy_grid", "boltz_collide", "boltz_relax",
                      "boltz_moments", "boltz_stream_status", "boltz_grid_info", "boltz_grid_tables",
-                     "boltz_relax_noalloc"):
+                     "boltz_relax_noalloc", "boltz_collide_indexed", "boltz_relax_indexed",
+                     "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
+                     "boltz_server_destroy"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -144,6 +155,17 @@ def boltz_relax_noalloc(batch: boltz_batch, f, dt: float, steps: int, stream=Non
     _check(lib().boltz_relax_noalloc(ctypes.byref(batch), _ptr(f), dt, steps, _stream(stream)))
 
 
+def boltz_collide_indexed(batch: boltz_batch, f, Q, cell_idx, pool_cells: int, stream=None) -> None:
+    _check(lib().boltz_collide_indexed(ctypes.byref(batch), _ptr(f), _ptr(Q), _ptr(cell_idx), pool_cells,
+                                       _stream(stream)))
+
+
+def boltz_relax_indexed(batch: boltz_batch, f, cell_idx, pool_cells: int, dt: float, steps: int,
+                        stream=None) -> None:
+    _check(lib().boltz_relax_indexed(ctypes.byref(batch), _ptr(f), _ptr(cell_idx), pool_cells, dt, steps,
+                                     _stream(stream)))
+
+
 def boltz_moments(batch: boltz_batch, f, U, stream=None) -> None:
     _check(lib().boltz_moments(ctypes.byref(batch), _ptr(f), _ptr(U), _stream(stream)))
 
@@ -184,6 +206,47 @@ def boltz_grid_tables(grid: int, M_dirs: int):
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(lib().boltz_grid_tables(grid, p(e), p(w), p(al), p(ap), p(D)))
     return e.reshape(M_dirs, 3), w, al.reshape(Me, N, N, N), ap.reshape(Me, N, N, N), D.reshape(N, N, N)
+
+
+class Server:
+    """Continuous-batching relaxation server (boltz_server_*): one pool per grid."""
+
+    def __init__(self, grids, prec: int, dt: float, hbm_budget_bytes: int, stream=None):
+        arr = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
+        h = ctypes.c_void_p()
+        _check(lib().boltz_server_create(arr, len(grids), prec, dt, hbm_budget_bytes, _stream(stream),
+                                         ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = []  # host buffers stay alive until their job is done
+
+    def submit(self, grid_index: int, f_host, out_host, steps: int) -> int:
+        jid = ctypes.c_int64()
+        _check(lib().boltz_server_submit(self.handle, grid_index, _ptr(f_host), _ptr(out_host), steps,
+                                         ctypes.byref(jid)))
+        self._keep.append((f_host, out_host))
+        return jid.value
+
+    def step(self):
+        r, q = ctypes.c_int(), ctypes.c_int()
+        _check(lib().boltz_server_step(self.handle, ctypes.byref(r), ctypes.byref(q)))
+        return r.value, q.value
+
+    def poll(self, job_id: int) -> bool:
+        d = ctypes.c_int()
+        _check(lib().boltz_server_poll(self.handle, job_id, ctypes.byref(d)))
+        return bool(d.value)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            boltz_destroy_server = lib().boltz_server_destroy
+            _check(boltz_destroy_server(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Grid:

@@ -182,6 +182,72 @@ boltz_status boltz_collide(const boltz_batch* b, const void* f, void* Q, void* s
                                b->grid->project, (cudaStream_t)stream);
 }
 
+boltz_status boltz_collide_indexed(const boltz_batch* b, const void* f, void* Q, const int64_t* cell_idx,
+                                   int64_t pool_cells, void* stream) {
+  boltz_status st = check_batch(b);
+  if (st != BOLTZ_OK) return st;
+  if (b->n_cells == 0) return BOLTZ_OK;
+  if (!f || !Q || !cell_idx) {
+    set_error("null f, Q or cell_idx");
+    return BOLTZ_EINVAL;
+  }
+  if (f == Q) {
+    set_error("f and Q must not overlap");
+    return BOLTZ_EINVAL;
+  }
+  if (pool_cells < 1 || pool_cells > ((int64_t)1 << 31)) {
+    set_error("pool_cells must lie in [1, 2^31]");
+    return BOLTZ_EINVAL;
+  }
+  if ((st = check_device(b->grid)) != BOLTZ_OK) return st;
+  return boltz::launch_collide(b->grid, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, Q, 0.0, 0.0, 1.0, nullptr, 0,
+                               b->grid->project, (cudaStream_t)stream, cell_idx, pool_cells);
+}
+
+boltz_status boltz_relax_indexed(const boltz_batch* b, void* f, const int64_t* cell_idx, int64_t pool_cells,
+                                 double dt, int steps, void* stream) {
+  boltz_status st = check_batch(b);
+  if (st != BOLTZ_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) {
+    set_error("dt must be positive and finite");
+    return BOLTZ_EINVAL;
+  }
+  if (steps < 0) {
+    set_error("steps must be >= 0");
+    return BOLTZ_EINVAL;
+  }
+  if (b->n_cells == 0 || steps == 0) return BOLTZ_OK;
+  if (!f || !cell_idx) {
+    set_error("null f or cell_idx");
+    return BOLTZ_EINVAL;
+  }
+  if (pool_cells < 1 || pool_cells > ((int64_t)1 << 31)) {
+    set_error("pool_cells must lie in [1, 2^31]");
+    return BOLTZ_EINVAL;
+  }
+  if ((st = check_device(b->grid)) != BOLTZ_OK) return st;
+  boltz_grid_s* g = b->grid;
+  cudaStream_t s = (cudaStream_t)stream;
+  // moment targets per slot: scratch sized for the pool, grown on demand
+  if ((size_t)pool_cells > g->U0_cap) {
+    cudaStreamSynchronize(s);
+    cudaFree(g->U0);
+    g->U0 = nullptr;
+    g->U0_cap = 0;
+    if (cudaMalloc(&g->U0, (size_t)pool_cells * 5 * sizeof(double)) != cudaSuccess) {
+      set_error("relax scratch allocation failed");
+      return BOLTZ_ENOMEM;
+    }
+    g->U0_cap = (size_t)pool_cells;
+  }
+  for (int it = 0; it < steps; ++it) {
+    st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, g->U0,
+                               it == 0 ? 1 : 0, 1, s, cell_idx, pool_cells);
+    if (st != BOLTZ_OK) return st;
+  }
+  return BOLTZ_OK;
+}
+
 boltz_status boltz_moments(const boltz_batch* b, const void* f, double* U, void* stream) {
   if (!b || !b->grid || b->n_cells < 0 || (b->f_is_fp64 != 0 && b->f_is_fp64 != 1)) {
     set_error("bad batch");
@@ -271,6 +337,10 @@ boltz_status boltz_stream_status(void* stream) {
   unsigned v = 0;
   boltz_status st = boltz::read_and_clear_status((cudaStream_t)stream, &v);
   if (st != BOLTZ_OK) return st;
+  if (v & 4u) {
+    set_error("a cell index was outside its pool (that cell was not written)");
+    return BOLTZ_EINVAL;
+  }
   if (v & 1u) {
     set_error("a non-finite value was produced on the device");
     return BOLTZ_ENONFINITE;

@@ -54,11 +54,14 @@ struct CollideArgs {
   int M_eff;
   int project;
   int compute_targets; // 1: targets = Phi f_in, computed here and written to Utgt if non-null
+  const int64_t* cell_idx;  // null: cell c of the launch is slot c; else slot cell_idx[c]
+  int64_t pool_cells;       // number of slots behind f_in / f_base / out / Utgt (cell_idx)
   KernelGeom geom;
 };
 
 // Status bits of g_boltz_status.
 constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusBadIndex = 4u;
 
 template <typename T, int N, int C>
 struct CollideCfg {
@@ -176,7 +179,16 @@ collide_kernel(const CollideArgs args) {
   double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
 
   const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
-  const long long cell = blockIdx.x / C;
+  // Slot of this cell.  An index outside [0, pool_cells) is reported; the cell then
+  // reads slot 0 and writes nothing, so every CTA still runs the same barrier sequence.
+  long long cell = blockIdx.x / C;
+  bool writable = true;
+  if (args.cell_idx) {
+    const long long s = args.cell_idx[cell];
+    writable = (s >= 0 && s < args.pool_cells);
+    if (!writable && threadIdx.x == 0) atomicOr(&g_boltz_status, kStatusBadIndex);
+    cell = writable ? s : 0;
+  }
   const int t = threadIdx.x;
   // spectral passes: thread (kyl, kz), lanes along kz
   const int kyl = t / N, kzt = t % N;
@@ -419,7 +431,7 @@ collide_kernel(const CollideArgs args) {
 #pragma unroll
       for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
     }
-    if (args.compute_targets && args.Utgt && rank == 0 && t < 5) args.Utgt[cell * 5 + t] = tgt[t];
+    if (args.compute_targets && args.Utgt && writable && rank == 0 && t < 5) args.Utgt[cell * 5 + t] = tgt[t];
     double rhs[5];
 #pragma unroll
     for (int r = 0; r < 5; ++r) rhs[r] = tgt[r] - tot[r];
@@ -442,7 +454,7 @@ collide_kernel(const CollideArgs args) {
   for (int y = 0; y < N; ++y) {
     const double val = g[y] + (P0 + (double)y * (P1 + (double)y * P2));
     bad |= !isfinite(val);
-    out[(x * N + y) * N + z] = (TIO)val;
+    if (writable) out[(x * N + y) * N + z] = (TIO)val;
   }
   if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
 }
@@ -608,7 +620,8 @@ static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int6
 
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, const void* f_in,
                             const void* f_base, void* out, double a, double b, double s, double* Utgt,
-                            int compute_targets, int project, cudaStream_t stream) {
+                            int compute_targets, int project, cudaStream_t stream, const int64_t* cell_idx,
+                            int64_t pool_cells) {
   if (n_cells == 0) return BOLTZ_OK;
   if (!collide_supported(g->N, prec)) {
     set_error("unsupported (N, precision) combination");
@@ -626,6 +639,8 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.M_eff = g->M_eff;
   args.project = project;
   args.compute_targets = compute_targets;
+  args.cell_idx = cell_idx;
+  args.pool_cells = pool_cells;
   args.geom.L = g->L;
   args.geom.dv = g->dv;
   for (int i = 0; i < 25; ++i) args.geom.G[i] = g->proj.G[i];

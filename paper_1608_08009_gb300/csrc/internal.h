@@ -61,7 +61,8 @@ boltz_status upload_tables(boltz_grid_s* g);
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64,
                             const void* f_in, const void* f_base, void* out, double a, double b,
                             double s, double* Utgt, int compute_targets, int project,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const int64_t* cell_idx = nullptr,
+                            int64_t pool_cells = 0);
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
                             double* U, double scale, cudaStream_t stream);
 bool collide_supported(int N, int prec);

@@ -228,3 +228,37 @@ def test_full_size_fp64_sampled():
         sample = [0, 1, 2047, 4095]
         Qref = O.collide(W.two_maxwellians(n_cells, N, L, seed, cells=sample), oracle_grid(N, L, M))
         assert rel_l2(Q[sample].cpu().numpy(), Qref) <= 1e-12
+
+
+def test_indexed_cells_match_contiguous_batch():
+    N, L, M, pool = 16, 6.0, 16, 9
+    f = W.two_maxwellians(pool, N, L, seed=61)
+    with B.Grid(N, L, 1.0, M) as g:
+        fd = torch.from_numpy(f).cuda()
+        Qfull = torch.empty_like(fd)
+        B.boltz_collide(g.batch(pool), fd, Qfull)
+        idx = torch.tensor([7, 2, 5, 0], dtype=torch.int64, device="cuda")
+        Q = torch.zeros_like(fd)
+        B.boltz_collide_indexed(g.batch(4), fd, Q, idx, pool)
+        B.boltz_stream_status()
+        sel = idx.cpu().numpy()
+        assert torch.equal(Q[sel], Qfull[sel])
+        untouched = [c for c in range(pool) if c not in sel]
+        assert torch.count_nonzero(Q[untouched]).item() == 0
+        # relax of the listed slots only
+        ft = fd.clone()
+        B.boltz_relax_indexed(g.batch(4), ft, idx, pool, 0.004, 2)
+        ref = fd[sel].clone()
+        B.boltz_relax(g.batch(4), ref, 0.004, 2, 1)
+        B.boltz_stream_status()
+        assert torch.equal(ft[sel], ref)
+        assert torch.equal(ft[untouched], fd[untouched])
+        # an index outside the pool is reported and nothing is written for it
+        bad = torch.tensor([1, pool + 3], dtype=torch.int64, device="cuda")
+        Q2 = torch.zeros_like(fd)
+        B.boltz_collide_indexed(g.batch(2), fd, Q2, bad, pool)
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_stream_status()
+        assert ei.value.status == B.BOLTZ_EINVAL
+        assert torch.equal(Q2[1], Qfull[1])
+        assert torch.count_nonzero(Q2[[c for c in range(pool) if c != 1]]).item() == 0
