@@ -45,7 +45,31 @@ import numpy as np  # noqa: E402
 WORKLOADS = {
     "mixed32": dict(cells=32768, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20163),
     "fp64_32": dict(cells=4096, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp64", f64=True, seed=20162),
+    # one cell, Maxwell molecules through the rank-16 radial expansion, 32 spherical-
+    # Fibonacci directions, 3D BKW datum at K = 3/5 on the box of support radius 6,
+    # one Heun step (two collision evaluations) per bench step
+    "bkw16": dict(cells=1, N=16, L=(3.0 + math.sqrt(2.0)) * 3.0, M=32, gamma=0.0, dt=0.01, prec="fp64", f64=True,
+                  seed=20161, rk=2, init="bkw",
+                  opts=dict(dirs_kind=1, C_gamma=1.0 / (4.0 * math.pi), radial_rank=16)),
 }
+L2_BYTES = 126 << 20  # GB300 L2 as reported by the device; inputs below 2x this flush L2 between steps
+
+
+def bkw_K(t: float) -> float:
+    """Shape parameter of the 3D BKW solution at time t (K(t) = 1 - exp(-t / 6))."""
+    return 1.0 - math.exp(-t / 6.0)
+
+
+BKW_T0 = -6.0 * math.log(1.0 - 0.6)  # K(t0) = 3/5
+
+
+def make_inputs(wl: dict, cells, total: int):
+    """Seeded inputs of the workload for the listed cells of a batch of `total` cells."""
+    from paper_1608_08009_gb300 import workloads as W
+
+    if wl.get("init") == "bkw":
+        return np.repeat(W.bkw(wl["N"], wl["L"], bkw_K(BKW_T0))[None], len(cells), axis=0)
+    return W.two_maxwellians(total, wl["N"], wl["L"], wl["seed"], cells=cells)
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor), nominal
 # DRAM bytes (read + write) per cell of one collide_kernel launch, from one ncu capture of
@@ -150,16 +174,22 @@ def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096):
     import oracle as O
     from paper_1608_08009_gb300 import workloads as W
 
-    g = O.make_grid(wl["N"], wl["L"], gamma=wl["gamma"], M=wl["M"])
+    o = wl.get("opts", {})
+    g = O.make_grid(wl["N"], wl["L"], gamma=wl["gamma"], M=wl["M"], dirs_kind=o.get("dirs_kind", 0),
+                    C_gamma=o.get("C_gamma", 1.0), rank=o.get("radial_rank") or None)
+    rk = wl.get("rk", 1)
     U_done, t0 = 0, time.perf_counter()
     c = 0
     while c < max_cells:
-        f = W.two_maxwellians(wl["cells"], wl["N"], wl["L"], wl["seed"], cells=[c])
-        U0 = O.moments(f, g)
-        Q = O.collide(f, g, project=False)
-        O.project_f(f + wl["dt"] * Q, U0, g)
+        f = make_inputs(wl, [c], wl["cells"])
+        if rk == 1:
+            U0 = O.moments(f, g)
+            Q = O.collide(f, g, project=False)
+            O.project_f(f + wl["dt"] * Q, U0, g)
+        else:
+            O.relax(f, g, wl["dt"], 1, rk_order=rk)
         c += 1
-        U_done += 1
+        U_done += rk
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
@@ -272,22 +302,36 @@ def run_reference(args, wl):
     line = {
         "impl": "reference", "metric": "cell-collisions/s", "value": value, "unit": "cell-collisions/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * wl["cells"] / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000.0 * wl["cells"] * wl.get("rk", 1) / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args, wl),
         "cpu_baseline": {"value": value, "unit": "cell-collisions/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{cells_total} cells of the workload over {args.steps} steps, FP64 numpy oracle"},
+                         "sample": f"{cells_total} cell-collisions of the workload over {args.steps} steps, FP64 numpy oracle"},
         "e2e": {"value": value, "unit": "cell-collisions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+def l2_policy(wl: dict) -> str:
+    nbytes = wl["cells"] * wl["N"] ** 3 * (8 if wl["f64"] else 4)
+    if nbytes >= 2 * L2_BYTES:
+        return "inputs larger than L2 (f is %.1f GB)" % (nbytes / 1e9)
+    return "L2 flushed between timed steps (f is %.1f MB)" % (nbytes / 1e6)
+
+
 def config_of(args, wl):
+    o = wl.get("opts", {})
+    dirs = {0: "product grid of midpoints", 1: "spherical Fibonacci", 2: "Gauss x midpoint"}[o.get("dirs_kind", 0)]
+    extra = {}
+    if wl.get("rk", 1) == 2:
+        extra["integrator"] = "Heun (2 collision evaluations per step)"
+    if wl.get("init") == "bkw":
+        extra["datum"] = "3D BKW at K = 3/5, Maxwell molecules, B = 1/(4 pi), radial rank %d" % o.get("radial_rank", 16)
     return {"workload": args.workload, "cells_per_gpu": wl["cells"], "N_v": wl["N"], "L": wl["L"], "M_dirs": wl["M"],
-            "gamma": wl["gamma"], "dirs": "8x8 product grid", "dt": wl["dt"], "precision": wl["prec"],
+            "gamma": wl["gamma"], "dirs": dirs, "dt": wl["dt"], "precision": wl["prec"], **extra,
             "f_storage": "f64" if wl["f64"] else "f32", "moments_projection_update": "f64",
-            "l2_policy": "inputs larger than L2 (f is %.1f GB)" % (wl["cells"] * wl["N"] ** 3 * (8 if wl["f64"] else 4) / 1e9),
+            "l2_policy": l2_policy(wl),
             "parallelism": f"cells sharded, {args.gpus} GPU(s)"}
 
 
@@ -306,18 +350,22 @@ def run_ours(args, wl):
     N, L, M, cells = wl["N"], wl["L"], wl["M"], wl["cells"]
     prec = B.BOLTZ_FP64 if wl["prec"] == "fp64" else B.BOLTZ_FP32_FFT
     dtype = torch.float64 if wl["f64"] else torch.float32
-    grid = B.Grid(N, L, wl["gamma"], M)
+    grid = B.Grid(N, L, wl["gamma"], M, **wl.get("opts", {}))
     batch = grid.batch(cells, prec, wl["f64"])
+    rk = wl.get("rk", 1)
     # seeded inputs; rank r takes the cells [r * cells, (r+1) * cells) of one big batch
     host = torch.empty(cells, N, N, N, dtype=dtype).pin_memory()
     chunk = 1024
     for c0 in range(0, cells, chunk):
         c1 = min(cells, c0 + chunk)
         mine = shard_cells(rank, cells)
-        host[c0:c1] = torch.from_numpy(W.two_maxwellians(cells * ws, N, L, wl["seed"], cells=mine[c0:c1]))
+        host[c0:c1] = torch.from_numpy(make_inputs(wl, mine[c0:c1], cells * ws))
     f0 = host.cuda()
     f = f0.clone()
     stream = torch.cuda.current_stream()
+    # inputs smaller than L2: flush it between timed steps (outside the step's events)
+    nbytes = host.numel() * host.element_size()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if nbytes < 2 * L2_BYTES else None
 
     def barrier():
         torch.cuda.synchronize()
@@ -328,7 +376,7 @@ def run_ours(args, wl):
 
     # ---- device-resident timing --------------------------------------------------------
     for _ in range(args.warmup):
-        B.boltz_relax(batch, f, wl["dt"], 1, 1, stream)
+        B.boltz_relax(batch, f, wl["dt"], 1, rk, stream)
     B.boltz_stream_status(stream)
     f.copy_(f0)
     barrier()
@@ -341,17 +389,20 @@ def run_ours(args, wl):
     barrier()
     t_start.record(stream)
     for k in range(args.steps):
+        if flush is not None:
+            flush.zero_()
         ev[k][0].record(stream)
-        B.boltz_relax(batch, f, wl["dt"], 1, 1, stream)
+        B.boltz_relax(batch, f, wl["dt"], 1, rk, stream)
         ev[k][1].record(stream)
     t_end.record(stream)
     barrier()
     clocks = sampler.stop()
     B.boltz_stream_status(stream)
-    total_ms = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    # with L2 flushes between steps the timed region is the sum of the steps' own events
+    total_ms = sum(step_ms) if flush is not None else t_start.elapsed_time(t_end)
     total_ms = max_over_ranks(total_ms, "cuda")
-    value = cells * ws * args.steps / (total_ms / 1000.0)
+    value = cells * ws * args.steps * rk / (total_ms / 1000.0)
 
     # drift of the conserved moments over the timed steps, on the stored state
     U0 = torch.empty(cells, 5, dtype=torch.float64, device="cuda")
@@ -359,7 +410,10 @@ def run_ours(args, wl):
     B.boltz_moments(batch, f0, U0, stream)
     B.boltz_moments(batch, f, U1, stream)
     B.boltz_stream_status(stream)
-    drift = ((U1 - U0).abs().max(dim=0).values / U0.abs().max(dim=0).values).cpu().tolist()
+    # per cell, momentum is scaled by sqrt(2 rho E) >= |rho u| (a cell at rest has zero momentum)
+    scale = U0.abs().clone()
+    scale[:, 1:4] = torch.sqrt(2.0 * U0[:, :1] * U0[:, 4:5]).expand(-1, 3)
+    drift = ((U1 - U0).abs() / scale).max(dim=0).values.cpu().tolist()
 
     # ---- end to end through the public API with host buffers ----------------------------
     out_host = torch.empty_like(host).pin_memory()
@@ -370,20 +424,44 @@ def run_ours(args, wl):
     e0.record(stream)
     for _ in range(e2e_steps):
         f.copy_(host, non_blocking=True)
-        B.boltz_relax(batch, f, wl["dt"], 1, 1, stream)
+        B.boltz_relax(batch, f, wl["dt"], 1, rk, stream)
         out_host.copy_(f, non_blocking=True)
     e1.record(stream)
     barrier()
     B.boltz_stream_status(stream)
     e2e_ms = e0.elapsed_time(e1)
     e2e_ms = max_over_ranks(e2e_ms, "cuda")
-    e2e_value = cells * ws * e2e_steps / (e2e_ms / 1000.0)
-    nbytes = host.numel() * host.element_size()
+    e2e_value = cells * ws * e2e_steps * rk / (e2e_ms / 1000.0)
 
     # accuracy of this path on the whole batch: Q(f0) against the float64 GPU path (itself
     # pinned to the oracle at ~1e-13), relative L2 over all cells and velocities
     err = None
+    err_steps = None
+    bkw_err = None
+    if wl.get("init") == "bkw":
+        # distance to the exact BKW solution after each of 10 Heun steps from t0
+        from paper_1608_08009_gb300 import workloads as W
+
+        fb = f0.clone()
+        bkw_err = []
+        for k in range(10):
+            B.boltz_relax(batch, fb, wl["dt"], 1, rk, stream)
+            ex = torch.from_numpy(W.bkw(N, L, bkw_K(BKW_T0 + wl["dt"] * (k + 1)))).to(fb)
+            bkw_err.append(((fb[0] - ex).norm() / ex.norm()).item())
+        B.boltz_stream_status(stream)
     if wl["prec"] != "fp64" and not args.no_accuracy:
+        # 20 Euler steps of the float32 path and of the float64 path from the same f0 on a
+        # 512-cell subset: relative L2 distance of the states after each step
+        sub = min(cells, 512)
+        a = f0[:sub].clone()
+        b64 = f0[:sub].double()
+        err_steps = []
+        for _ in range(20):
+            B.boltz_relax(grid.batch(sub, prec, False), a, wl["dt"], 1, 1, stream)
+            B.boltz_relax(grid.batch(sub, B.BOLTZ_FP64, True), b64, wl["dt"], 1, 1, stream)
+            err_steps.append(((a.double() - b64).norm() / b64.norm()).item())
+        B.boltz_stream_status(stream)
+        del a, b64
         Qx = torch.empty_like(f0)
         B.boltz_collide(batch, f0, Qx, stream)
         f64 = f0.double()
@@ -395,8 +473,8 @@ def run_ours(args, wl):
 
     if rank == 0:
         peaks = measured_peaks()
-        flops_cell = algorithmic_flops(N, M)
-        avg_s = statistics.mean(step_ms) / 1000.0
+        flops_cell = algorithmic_flops(N, grid.info["M_eff"])
+        avg_s = statistics.mean(step_ms) / 1000.0 / rk  # one launch per collision evaluation
         achieved = flops_cell * cells / avg_s / 1e12
         if wl["prec"] == "fp64":
             peak, peak_note = NOMINAL_FP64_TFLOPS, "nominal FP64 ALU 1.25 TFLOP/s"
@@ -417,8 +495,10 @@ def run_ours(args, wl):
                          "flops_per_cell": flops_cell, "peak_source": peak_note},
             "e2e": {"value": e2e_value, "unit": "cell-collisions/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * rk,
             "err_vs_fp64": err,
+            "err_vs_fp64_per_step": err_steps,
+            "err_vs_bkw_exact_per_step": bkw_err,
             "clocks": clocks,
             "moment_drift_rel": drift,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
