@@ -416,16 +416,17 @@ def run_ours(args, wl):
     drift = ((U1 - U0).abs() / scale).max(dim=0).values.cpu().tolist()
 
     # ---- end to end through the public API with host buffers ----------------------------
+    # boltz_relax_host: every step uploads f from pinned host memory, runs the step and
+    # downloads the result, copies pipelined with the compute chunk by chunk
     out_host = torch.empty_like(host).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
+    B.boltz_relax_host(batch, host, out_host, wl["dt"], 1, rk, 0, stream)  # staging set up outside the timing
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        f.copy_(host, non_blocking=True)
-        B.boltz_relax(batch, f, wl["dt"], 1, rk, stream)
-        out_host.copy_(f, non_blocking=True)
+        B.boltz_relax_host(batch, host, out_host, wl["dt"], 1, rk, 0, stream)
     e1.record(stream)
     barrier()
     B.boltz_stream_status(stream)

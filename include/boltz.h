@@ -148,6 +148,22 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
  * EUNSUPPORTED, ECUDA. */
 boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, double dt, int steps, void* stream);
 
+/* boltz_relax for distributions in HOST memory (Sec. 3.1, Eq. relax; the steps are those
+ * of boltz_relax).  f_in, f_out: host arrays of n_cells * N^3 elements (float32 or
+ * float64 per f_is_fp64), owned by the caller; they may be the same array.  Page-locked
+ * memory (cudaHostAlloc / cudaHostRegister) lets the copies overlap the compute; pageable
+ * memory is accepted and serialises.  The batch runs in chunks of chunk_cells cells
+ * (0: about an eighth of the batch, at least 512 cells, at most 1 GiB of f): the upload
+ * of a chunk, the collision steps of the previous one and the download of the one
+ * before run concurrently on two library streams and `stream`.  Returns once the work
+ * is enqueued; `stream` is ordered after the last download, so synchronise it (or call
+ * boltz_stream_status) before reading f_out or reusing f_in.  The result equals
+ * boltz_relax on the same cells bit for bit.  Staging buffers (three chunks, a Heun
+ * stage and the chunk's moment targets) are owned by the grid and grown on demand; calls
+ * on one grid must not overlap.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+boltz_status boltz_relax_host(const boltz_batch* b, const void* f_in, void* f_out, double dt, int steps,
+                              int rk_order, int64_t chunk_cells, void* stream);
+
 /* Cells addressed through an index array (ragged batches, resident pools): cell c of the
  * call is slot cell_idx[c] of f (and of Q), with slot s at offset s * N^3.  cell_idx is a
  * device array of n_cells int64 values; slots must be distinct and lie in

@@ -35,7 +35,7 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_relax", "boltz_moments", "boltz_stream_status", "boltz_last_error",
             "boltz_grid_info", "boltz_grid_tables", "boltz_version", "boltz_relax_noalloc",
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
-            "boltz_server_step", "boltz_server_poll", "boltz_server_destroy")
+            "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host")
 
 
 class BoltzError(RuntimeError):
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_relax.argtypes = [P(boltz_batch), vp, f64, i32, i32, vp]
         L.boltz_moments.argtypes = [P(boltz_batch), vp, vp, vp]
         L.boltz_relax_noalloc.argtypes = [P(boltz_batch), vp, f64, i32, vp]
+        L.boltz_relax_host.argtypes = [P(boltz_batch), vp, vp, f64, i32, i32, i64, vp]
         L.boltz_collide_indexed.argtypes = [P(boltz_batch), vp, vp, vp, i64, vp]
         L.boltz_relax_indexed.argtypes = [P(boltz_batch), vp, vp, i64, f64, i32, vp]
         L.boltz_server_create.argtypes = [P(vp), i32, i32, f64, ctypes.c_size_t, vp, P(vp)]
@@ -93,7 +94,7 @@ def lib() -> ctypes.CDLL:
                      "boltz_moments", "boltz_stream_status", "boltz_grid_info", "boltz_grid_tables",
                      "boltz_relax_noalloc", "boltz_collide_indexed", "boltz_relax_indexed",
                      "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
-                     "boltz_server_destroy"):
+                     "boltz_server_destroy", "boltz_relax_host"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -153,6 +154,14 @@ def boltz_relax(batch: boltz_batch, f, dt: float, steps: int, rk_order: int = 1,
 def boltz_relax_noalloc(batch: boltz_batch, f, dt: float, steps: int, stream=None) -> None:
     """Forward-Euler relaxation with no allocation (scratch in a fixed device array)."""
     _check(lib().boltz_relax_noalloc(ctypes.byref(batch), _ptr(f), dt, steps, _stream(stream)))
+
+
+def boltz_relax_host(batch: boltz_batch, f_in, f_out, dt: float, steps: int, rk_order: int = 1,
+                     chunk_cells: int = 0, stream=None) -> None:
+    """boltz_relax on host (preferably pinned) buffers; copies pipelined with the compute.
+    Enqueued only: synchronise `stream` before reading f_out."""
+    _check(lib().boltz_relax_host(ctypes.byref(batch), _ptr(f_in), _ptr(f_out), dt, steps, rk_order, chunk_cells,
+                                  _stream(stream)))
 
 
 def boltz_collide_indexed(batch: boltz_batch, f, Q, cell_idx, pool_cells: int, stream=None) -> None:

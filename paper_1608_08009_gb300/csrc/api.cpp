@@ -19,7 +19,9 @@ boltz_status read_and_clear_status(cudaStream_t stream, unsigned* value);
 
 using boltz::set_error;
 
-static boltz_status check_batch(const boltz_batch* b) {
+namespace boltz {
+
+boltz_status check_batch(const boltz_batch* b) {
   if (!b || !b->grid) {
     set_error("null batch or grid");
     return BOLTZ_EINVAL;
@@ -47,7 +49,7 @@ static boltz_status check_batch(const boltz_batch* b) {
   return BOLTZ_OK;
 }
 
-static boltz_status check_device(const boltz_grid_s* g) {
+boltz_status check_device(const boltz_grid_s* g) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -60,6 +62,11 @@ static boltz_status check_device(const boltz_grid_s* g) {
   }
   return BOLTZ_OK;
 }
+
+}  // namespace boltz
+
+using boltz::check_batch;
+using boltz::check_device;
 
 extern "C" {
 
@@ -160,6 +167,7 @@ boltz_status boltz_destroy_grid(boltz_grid g) {
   cudaFree(g->w_dev);
   cudaFree(g->U0);
   cudaFree(g->stage);
+  boltz::free_host_pipeline(g);
   if (prev >= 0) cudaSetDevice(prev);
   delete g;
   return BOLTZ_OK;
@@ -313,25 +321,36 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
     }
     g->stage_cap = stage_bytes;
   }
+  return boltz::relax_steps(g, b->n_cells, b->prec, b->f_is_fp64, f, dt, steps, rk_order, s, g->U0, g->stage);
+}
+
+}  // extern "C"
+
+namespace boltz {
+
+boltz_status relax_steps(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, void* f, double dt,
+                         int steps, int rk_order, cudaStream_t s, double* U0, void* stage) {
+  boltz_status st;
   // Targets: Phi-sums of the initial state (Eq. minim1 with U fixed), computed by the
-  // first launch from the values it loads anyway and kept in g->U0 for the later ones.
+  // first launch from the values it loads anyway and kept in U0 for the later ones.
   for (int it = 0; it < steps; ++it) {
     const int first = (it == 0) ? 1 : 0;
     if (rk_order == 1) {
-      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, g->U0, first, 1,
-                                 s);
+      st = launch_collide(g, n_cells, prec, f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, U0, first, 1, s);
       if (st != BOLTZ_OK) return st;
     } else {
-      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, g->stage, 0.0, 1.0, dt, g->U0,
-                                 first, 1, s);
+      st = launch_collide(g, n_cells, prec, f_is_fp64, f, nullptr, stage, 0.0, 1.0, dt, U0, first, 1, s);
       if (st != BOLTZ_OK) return st;
-      st = boltz::launch_collide(g, b->n_cells, b->prec, b->f_is_fp64, g->stage, f, f, 0.5, 0.5, 0.5 * dt, g->U0,
-                                 0, 1, s);
+      st = launch_collide(g, n_cells, prec, f_is_fp64, stage, f, f, 0.5, 0.5, 0.5 * dt, U0, 0, 1, s);
       if (st != BOLTZ_OK) return st;
     }
   }
   return BOLTZ_OK;
 }
+
+}  // namespace boltz
+
+extern "C" {
 
 boltz_status boltz_stream_status(void* stream) {
   unsigned v = 0;

@@ -44,6 +44,18 @@ struct boltz_grid_s {
   size_t U0_cap = 0;  // cells
   void* stage = nullptr;
   size_t stage_cap = 0;  // bytes
+  // resources of boltz_relax_host (host_io.cpp), created on first use
+  static constexpr int kHostBufs = 3;
+  void* hbuf[kHostBufs] = {nullptr, nullptr, nullptr};  // device staging, one chunk each
+  size_t hbuf_cap = 0;                                   // bytes per buffer
+  double* hU0 = nullptr;                                 // [chunk][5]
+  void* hstage = nullptr;                                // Heun stage of one chunk
+  size_t hchunk_cap = 0;                                 // cells
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_in[kHostBufs] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_done[kHostBufs] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_out[kHostBufs] = {nullptr, nullptr, nullptr};
 };
 
 namespace boltz {
@@ -66,5 +78,13 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
                             double* U, double scale, cudaStream_t stream);
 bool collide_supported(int N, int prec);
+// `steps` Euler or Heun steps of n_cells cells of f in place (the body of boltz_relax);
+// U0: [n_cells][5] scratch for the targets, stage: one copy of f (Heun only).
+boltz_status relax_steps(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, void* f, double dt,
+                         int steps, int rk_order, cudaStream_t s, double* U0, void* stage);
+void free_host_pipeline(boltz_grid_s* g);
+// Argument checks shared by the entry points (api.cpp): set the error message on failure.
+boltz_status check_batch(const boltz_batch* b);
+boltz_status check_device(const boltz_grid_s* g);
 
 }  // namespace boltz
