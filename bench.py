@@ -50,7 +50,7 @@ WORKLOADS = {
     # one Heun step (two collision evaluations) per bench step
     "bkw16": dict(cells=1, N=16, L=(3.0 + math.sqrt(2.0)) * 3.0, M=32, gamma=0.0, dt=0.01, prec="fp64", f64=True,
                   seed=20161, rk=2, init="bkw",
-                  opts=dict(dirs_kind=1, C_gamma=1.0 / (4.0 * math.pi), radial_rank=16)),
+                  opts=dict(dirs_kind=1, C_gamma=1.0 / (4.0 * math.pi), radial_rank=16, term_groups=64)),
 }
 L2_BYTES = 126 << 20  # GB300 L2 as reported by the device; inputs below 2x this flush L2 between steps
 
@@ -197,7 +197,7 @@ def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096):
 
 
 def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_bytes: int = 2 << 30,
-                max_in_flight: int = 4) -> dict:
+                max_in_flight: int = 4, term_groups=None) -> dict:
     """Serving load (continuous batching through boltz_server_*): Poisson arrivals at
     `rate` req/s for `seconds`; each request is one cell relaxing for U{10..200} forward
     Euler steps, N in {16 (60 %), 32 (35 %), 64 (5 %)}, gamma = 1, M = 64, dt = 0.0025,
@@ -208,6 +208,7 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     from paper_1608_08009_gb300 import boltz as B
     from paper_1608_08009_gb300 import workloads as W
 
+    term_groups = term_groups or {16: 4, 32: 8}
     rng = np.random.Generator(np.random.PCG64(seed))
     n_req = int(rng.poisson(rate * seconds))
     arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
@@ -215,7 +216,9 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     steps = rng.integers(10, 201, size=n_req)
     # 16^3 jobs on [-6, 6)^3 (dv = 0.75), 32^3 jobs on [-8, 8)^3 (dv = 0.5)
     Ls = {16: 6.0, 32: 8.0}
-    grids = {N: B.Grid(N, Ls[N], 1.0, 64) for N in (16, 32)}
+    # term groups: a job's separated terms spread over several clusters, fixed per grid so
+    # a job's arithmetic does not depend on what else is resident
+    grids = {N: B.Grid(N, Ls[N], 1.0, 64, term_groups=term_groups[N]) for N in (16, 32)}
     gidx = {16: 0, 32: 1}
     stream = torch.cuda.current_stream()
     server = B.Server([grids[16], grids[32]], B.BOLTZ_FP32_FFT, 0.0025, budget_bytes, stream)
@@ -283,7 +286,8 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
             "cell_collisions_per_s": cell_steps / wall, "server_iterations": n_steps,
             "max_resident": max_res, "max_queued": max_q, "hbm_budget_bytes": budget_bytes,
             "mix": "N=16 (L=6): 60 %, N=32 (L=8): 35 %, N=64: 5 % (rejected); steps U{10..200}; M=64; "
-                   "gamma=1; dt=0.0025; f32"}
+                   "gamma=1; dt=0.0025; f32",
+            "term_groups": {str(k): v for k, v in term_groups.items()}}
 
 
 def run_reference(args, wl):
@@ -326,6 +330,8 @@ def config_of(args, wl):
     extra = {}
     if wl.get("rk", 1) == 2:
         extra["integrator"] = "Heun (2 collision evaluations per step)"
+    if o.get("term_groups", 1) > 1:
+        extra["term_groups"] = o["term_groups"]
     if wl.get("init") == "bkw":
         extra["datum"] = "3D BKW at K = 3/5, Maxwell molecules, B = 1/(4 pi), radial rank %d" % o.get("radial_rank", 16)
     return {"workload": args.workload, "cells_per_gpu": wl["cells"], "N_v": wl["N"], "L": wl["L"], "M_dirs": wl["M"],
@@ -505,7 +511,7 @@ def run_ours(args, wl):
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }
         if args.serve_seconds > 0 and ws == 1:
-            line["serve"] = run_serving(args.serve_seconds)
+            line["serve"] = run_serving(args.serve_seconds, term_groups=args.serve_groups)
         if not args.no_cpu_baseline and ws == 1:
             r, ncell, el = cpu_oracle_rate(wl, budget_s=args.cpu_budget)
             line["cpu_baseline"] = {"value": r, "unit": "cell-collisions/s", "cores": 1, "kind": "oracle",
@@ -531,10 +537,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the float64 comparison of the batch")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving-load window (0: skip)")
+    ap.add_argument("--serve-groups", type=str, default="",
+                    help="term groups of the serving grids, e.g. 16:4,32:8 (default)")
+    ap.add_argument("--term-groups", type=int, default=0, help="override the workload grid's term_groups")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.cells > 0:
         wl["cells"] = args.cells
+    if args.term_groups > 0:
+        wl["opts"] = dict(wl.get("opts", {}), term_groups=args.term_groups)
+    args.serve_groups = ({int(a): int(b) for a, b in (kv.split(":") for kv in args.serve_groups.split(","))}
+                         if args.serve_groups else None)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

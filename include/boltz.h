@@ -79,6 +79,14 @@ typedef struct {
                         <= 0: 1 for gamma == 1 (exact decoupling), 16 otherwise       */
   int inner_nodes;   /* Gauss-Legendre nodes of the inner radial integral, default 128 */
   int project;       /* 1 (default): apply the conservation projection to Q          */
+  int term_groups;   /* split each cell's separated terms over this many thread-block
+                        clusters (1 = default: one cluster per cell).  G > 1 lowers the
+                        latency of batches too small to fill the GPU at the cost of G - 1
+                        extra forward transforms per cell and a second launch that sums
+                        the partial gains and runs the epilogue; it needs device scratch
+                        of (G + 1) N^3 values per cell (grown on demand, kept with the
+                        grid).  Clamped to [1, M_eff].  Results depend on G (rounding
+                        order of the gain sum) but not on the batch size.               */
 } boltz_grid_opts;
 
 typedef struct boltz_grid_s* boltz_grid;

@@ -47,7 +47,7 @@ class BoltzError(RuntimeError):
 class boltz_grid_opts(ctypes.Structure):
     _fields_ = [("dirs_kind", ctypes.c_int), ("dirs_a1", ctypes.c_int), ("R_trunc", ctypes.c_double),
                 ("C_gamma", ctypes.c_double), ("radial_rank", ctypes.c_int), ("inner_nodes", ctypes.c_int),
-                ("project", ctypes.c_int)]
+                ("project", ctypes.c_int), ("term_groups", ctypes.c_int)]
 
 
 class boltz_batch(ctypes.Structure):

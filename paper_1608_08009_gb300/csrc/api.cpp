@@ -1,5 +1,6 @@
 // C ABI of libboltz (declared in include/boltz.h): argument checking, grid ownership,
 // relaxation driver.  All compute happens in the kernels of collide.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -78,6 +79,7 @@ void boltz_default_opts(boltz_grid_opts* o) {
   o->C_gamma = 1.0;
   o->radial_rank = 0;
   o->inner_nodes = 128;
+  o->term_groups = 1;
   o->project = 1;
 }
 
@@ -124,6 +126,10 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
     set_error("radial_rank 1 is exact only for gamma = 1");
     return BOLTZ_EINVAL;
   }
+  if (o.term_groups < 0 || o.term_groups > 4096) {
+    set_error("term_groups must lie in [0, 4096]");
+    return BOLTZ_EINVAL;
+  }
   boltz_grid_s* g = new (std::nothrow) boltz_grid_s();
   if (!g) {
     set_error("out of host memory");
@@ -145,6 +151,7 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
   g->a1 = o.dirs_a1;
   g->inner_nodes = o.inner_nodes;
   g->project = o.project ? 1 : 0;
+  g->term_groups = std::max(1, std::min(o.term_groups, M_dirs * rank));
   g->R = o.R_trunc > 0 ? o.R_trunc : 0.0;
   boltz_status st = boltz::build_tables(g);
   if (st == BOLTZ_OK) st = boltz::upload_tables(g);
@@ -167,6 +174,7 @@ boltz_status boltz_destroy_grid(boltz_grid g) {
   cudaFree(g->w_dev);
   cudaFree(g->U0);
   cudaFree(g->stage);
+  cudaFree(g->split_buf);
   boltz::free_host_pipeline(g);
   if (prev >= 0) cudaSetDevice(prev);
   delete g;

@@ -23,6 +23,8 @@
 // float64 for BOLTZ_FP64.  Moments, projection and the update are float64 in both.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "fft_regs.cuh"
@@ -56,6 +58,16 @@ struct CollideArgs {
   int compute_targets; // 1: targets = Phi f_in, computed here and written to Utgt if non-null
   const int64_t* cell_idx;  // null: cell c of the launch is slot c; else slot cell_idx[c]
   int64_t pool_cells;       // number of slots behind f_in / f_base / out / Utgt (cell_idx)
+  // Term groups.  groups = 1: one cluster per cell does every term and the epilogue.
+  // groups = G > 1: cluster (c, g) does the terms [g M_eff / G, (g + 1) M_eff / G) (the
+  // last group also the loss transform) and writes its partial gain to
+  // part[(c G + g) n ...] and the loss multiplier to loss[c n ...] (c = cell of the
+  // launch), then counts itself in arrivals[c]; the cluster that arrives last sums the
+  // partials in group order and runs the epilogue (and resets arrivals[c] to 0).
+  int groups;
+  void* part;          // [cells][G][n] T
+  void* loss;          // [cells][n] T
+  unsigned* arrivals;  // [cells], zero between launches
   KernelGeom geom;
 };
 
@@ -88,8 +100,10 @@ struct CollideCfg {
   static constexpr size_t XB = (size_t)NCH * N * RW * VEC;
   static constexpr size_t OFF_XB = FH * sizeof(T2);
   static constexpr size_t OFF_RED = OFF_XB + NXB * XB * sizeof(T2);
-  // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA
-  static constexpr size_t SMEM = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA; then
+  // the last-arrival flag of split launches
+  static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  static constexpr size_t SMEM = OFF_FLAG + 16;
   static_assert(THREADS % 32 == 0, "whole warps");
   static_assert(NP % VEC == 0, "whole chunks");
   static_assert(OFF_XB % 16 == 0 && (XB * sizeof(T2)) % 16 == 0, "16-byte aligned buffers");
@@ -164,7 +178,7 @@ __device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, dou
   re[0] = v.x; im[0] = v.y;
 }
 
-template <typename T, typename TIO, int N, int C>
+template <typename T, typename TIO, int N, int C, bool kSplit>
 __global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, 1)
 collide_kernel(const CollideArgs args) {
   using Cfg = CollideCfg<T, N, C>;
@@ -179,9 +193,17 @@ collide_kernel(const CollideArgs args) {
   double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
 
   const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  // Cell of the launch and term group of this cluster.
+  const int G = kSplit ? args.groups : 1;
+  long long lc = blockIdx.x / C;
+  int gi = 0;
+  if constexpr (kSplit) {
+    gi = (int)(lc % G);
+    lc /= G;
+  }
   // Slot of this cell.  An index outside [0, pool_cells) is reported; the cell then
   // reads slot 0 and writes nothing, so every CTA still runs the same barrier sequence.
-  long long cell = blockIdx.x / C;
+  long long cell = lc;
   bool writable = true;
   if (args.cell_idx) {
     const long long s = args.cell_idx[cell];
@@ -353,32 +375,81 @@ collide_kernel(const CollideArgs args) {
     }
   };
 
+  // This cluster's terms: i = 0 .. nt-1 is term j0 + i, and the loss transform (term
+  // M_eff) comes last in the last group (without a split: i = j = 0 .. M_eff).
+  const int j0 = kSplit ? (int)(((long long)gi * M_eff) / G) : 0;
+  const int j1 = kSplit ? (int)(((long long)(gi + 1) * M_eff) / G) : M_eff;
+  const bool has_loss = kSplit ? (gi == G - 1) : true;
+  const int nt = (j1 - j0) + (has_loss ? 1 : 0);
   if constexpr (kRegSpec) {
-    // Two x-plane buffers; term j uses buffer (j + 1) % 2.  The ky pass of term j - 1
-    // runs between the scatter of term j and the cluster barrier, so the remote stores
+    // Two x-plane buffers; term i uses buffer (i + 1) % 2.  The ky pass of term i - 1
+    // runs between the scatter of term i and the cluster barrier, so the remote stores
     // drain behind it.  It reads the other buffer, and every CTA finishes it before
-    // arriving, so no peer scatters term j + 1 into that buffer while it is read.
+    // arriving, so no peer scatters term i + 1 into that buffer while it is read.
     T w_prev = T(0);
-    for (int j = 0; j <= M_eff; ++j) {
-      T2* XBj = XB0 + ((j + 1) & 1) * Cfg::XB;
+    for (int i = 0; i < nt; ++i) {
+      const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
+      T2* XBj = XB0 + ((i + 1) & 1) * Cfg::XB;
       const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
       pass_kx(j, XBj);
-      if (j > 0) pass_ky(XB0 + (j & 1) * Cfg::XB, w_prev, true);
+      if (i > 0) pass_ky(XB0 + (i & 1) * Cfg::XB, w_prev, true);
       cluster_barrier<C>();
       pass_kz(XBj);
       __syncthreads();
       w_prev = wj;
     }
-    pass_ky(XB0 + ((M_eff + 1) & 1) * Cfg::XB, T(0), false);  // loss term
+    // last term: the loss transform (re[] keeps L) or a gain term
+    if (has_loss) {
+      pass_ky(XB0 + (nt & 1) * Cfg::XB, T(0), false);
+    } else {
+      pass_ky(XB0 + (nt & 1) * Cfg::XB, w_prev, true);
+    }
   } else {
-    for (int j = 0; j <= M_eff; ++j) {
+    for (int i = 0; i < nt; ++i) {
+      const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
       const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
       pass_kx(j, XB0);
       cluster_barrier<C>();
       pass_kz(XB0);
       __syncthreads();
       pass_ky(XB0, wj, j < M_eff);
-      if (j < M_eff) cluster_barrier<C>();  // single buffer: owners done before the next scatter
+      if (i < nt - 1) cluster_barrier<C>();  // single buffer: owners done before the next scatter
+    }
+  }
+
+  if constexpr (kSplit) {
+    // Partial gain (and the loss multiplier) of this group, then the last-arrival count
+    // of the cell (fence, barrier, one atomic: no waiting).  The cluster that arrives last
+    // sums the G partials in group order, so the result does not depend on the order of
+    // arrival, and continues with the epilogue; the others leave.
+    T* part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
+    T* lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x_own * N + y) * N + zt;
+      part[(size_t)gi * n + idx] = acc[y];
+      if (has_loss) lossp[idx] = re[y];
+    }
+    __threadfence();
+    cluster_barrier<C>();
+    unsigned* flag = reinterpret_cast<unsigned*>(smem_raw + Cfg::OFF_FLAG);
+    if (rank == 0 && t == 0) {
+      const unsigned prev = atomicAdd(&args.arrivals[lc], 1u);
+      const unsigned last = (prev == (unsigned)(G - 1)) ? 1u : 0u;
+      if (last) args.arrivals[lc] = 0u;  // every group has arrived: ready for the next launch
+#pragma unroll
+      for (int q = 0; q < C; ++q) *cta_smem<C>(flag, q) = last;
+    }
+    cluster_barrier<C>();
+    if (*flag == 0u) return;  // the whole cluster leaves together
+    __threadfence();
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x_own * N + y) * N + zt;
+      T sum = __ldcg(part + idx);
+      for (int g2 = 1; g2 < G; ++g2) sum += __ldcg(part + (size_t)g2 * n + idx);
+      acc[y] = sum;
+      re[y] = __ldcg(lossp + idx);
     }
   }
 
@@ -431,7 +502,11 @@ collide_kernel(const CollideArgs args) {
 #pragma unroll
       for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
     }
-    if (args.compute_targets && args.Utgt && writable && rank == 0 && t < 5) args.Utgt[cell * 5 + t] = tgt[t];
+    if (args.compute_targets && args.Utgt && writable && rank == 0) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        if (t == r) args.Utgt[cell * 5 + r] = tgt[r];  // constant register index
+    }
     double rhs[5];
 #pragma unroll
     for (int r = 0; r < 5; ++r) rhs[r] = tgt[r] - tot[r];
@@ -578,7 +653,7 @@ boltz_status upload_tables(boltz_grid_s* g) {
 template <typename T, typename TIO, int N, int C>
 static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
   using Cfg = CollideCfg<T, N, C>;
-  auto kern = collide_kernel<T, TIO, N, C>;
+  auto kern = (a.groups > 1) ? collide_kernel<T, TIO, N, C, true> : collide_kernel<T, TIO, N, C, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   if (C > 1) {
@@ -586,7 +661,7 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(n_cells * C), 1, 1);
+  cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
   cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
   cfg.dynamicSmemBytes = Cfg::SMEM;
   cfg.stream = st;
@@ -621,11 +696,40 @@ static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int6
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, const void* f_in,
                             const void* f_base, void* out, double a, double b, double s, double* Utgt,
                             int compute_targets, int project, cudaStream_t stream, const int64_t* cell_idx,
-                            int64_t pool_cells) {
+                            int64_t pool_cells, int groups) {
   if (n_cells == 0) return BOLTZ_OK;
   if (!collide_supported(g->N, prec)) {
     set_error("unsupported (N, precision) combination");
     return BOLTZ_EUNSUPPORTED;
+  }
+  int G = groups < 0 ? g->term_groups : groups;
+  G = std::max(1, std::min(G, g->M_eff));
+  if (n_cells * (int64_t)G * 8 > (int64_t)INT32_MAX) {
+    set_error("n_cells * term_groups too large for one launch");
+    return BOLTZ_EINVAL;
+  }
+  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t tsz = (prec == BOLTZ_FP64) ? sizeof(double) : sizeof(float);
+  // scratch of split launches: [cells] arrival counters (zeroed once; each launch leaves
+  // them at zero), then the partial gains and the loss multipliers
+  const size_t cnt_bytes = ((size_t)n_cells * sizeof(unsigned) + 255) / 256 * 256;
+  if (G > 1) {
+    const size_t need = cnt_bytes + (size_t)n_cells * (G + 1) * n * tsz;
+    if (need > g->split_cap) {
+      // the old buffer may still be read by work queued on this stream
+      cudaError_t e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return cuda_fail(e, "split scratch sync");
+      cudaFree(g->split_buf);
+      g->split_buf = nullptr;
+      g->split_cap = 0;
+      if (cudaMalloc(&g->split_buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("split scratch allocation failed");
+        return BOLTZ_ENOMEM;
+      }
+      if ((e = cudaMemset(g->split_buf, 0, need)) != cudaSuccess) return cuda_fail(e, "split scratch clear");
+      g->split_cap = need;
+    }
   }
   CollideArgs args;
   args.f_in = f_in;
@@ -644,6 +748,11 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.geom.L = g->L;
   args.geom.dv = g->dv;
   for (int i = 0; i < 25; ++i) args.geom.G[i] = g->proj.G[i];
+  args.groups = G;
+  char* sb = static_cast<char*>(g->split_buf);
+  args.arrivals = (G > 1) ? reinterpret_cast<unsigned*>(sb) : nullptr;
+  args.part = (G > 1) ? sb + cnt_bytes : nullptr;
+  args.loss = (G > 1) ? sb + cnt_bytes + (size_t)n_cells * G * n * tsz : nullptr;
   if (prec == BOLTZ_FP64) {
     args.tab = g->tab64;
     return f_is_fp64 ? dispatch_n<double, double>(g, args, n_cells, stream)

@@ -31,6 +31,7 @@ struct boltz_grid_s {
   double L = 0, dv = 0, S = 0, R = 0, gamma = 1, C_gamma = 1;
   int M = 0, rank = 1, M_eff = 0;
   int dirs_kind = 0, a1 = 0, inner_nodes = 128, project = 1;
+  int term_groups = 1;  // clusters per cell sharing its separated terms (1 = no split)
   int device = 0;
   // float64 host tables, mode storage order (kx, ky, kz), kz fastest
   std::vector<double> e, wdir, w, alpha, alphap, D;
@@ -44,6 +45,9 @@ struct boltz_grid_s {
   size_t U0_cap = 0;  // cells
   void* stage = nullptr;
   size_t stage_cap = 0;  // bytes
+  // partial gains and loss of split launches (term_groups > 1), grown on demand
+  mutable void* split_buf = nullptr;
+  mutable size_t split_cap = 0;  // bytes
   // resources of boltz_relax_host (host_io.cpp), created on first use
   static constexpr int kHostBufs = 3;
   void* hbuf[kHostBufs] = {nullptr, nullptr, nullptr};  // device staging, one chunk each
@@ -74,7 +78,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                             const void* f_in, const void* f_base, void* out, double a, double b,
                             double s, double* Utgt, int compute_targets, int project,
                             cudaStream_t stream, const int64_t* cell_idx = nullptr,
-                            int64_t pool_cells = 0);
+                            int64_t pool_cells = 0, int groups = -1);  // groups < 0: the grid's term_groups
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
                             double* U, double scale, cudaStream_t stream);
 bool collide_supported(int N, int prec);

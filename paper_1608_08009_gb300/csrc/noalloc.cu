@@ -103,8 +103,9 @@ extern "C" boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, doubl
   st = boltz::launch_phisums(b->grid, b->n_cells, b->f_is_fp64, f, targets, 1.0, s);
   if (st != BOLTZ_OK) return st;
   for (int it = 0; it < steps; ++it) {
+    // groups = 1: a split launch would need the grid's scratch buffer
     st = boltz::launch_collide(b->grid, b->n_cells, b->prec, b->f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, targets, 0,
-                               1, s);
+                               1, s, nullptr, 0, 1);
     if (st != BOLTZ_OK) return st;
   }
   return BOLTZ_OK;

@@ -332,3 +332,49 @@ def test_relax_host_equals_device_relax(rk):
             B.boltz_relax_host(g.batch(cells, prec, fp64), inplace, inplace, 0.004, 2, rk)
             B.boltz_stream_status()
             assert torch.equal(inplace, ref)
+
+
+@pytest.mark.parametrize("N,L,M,groups", [(16, 6.0, 16, 2), (16, 6.0, 16, 5), (16, 6.0, 16, 16), (32, 8.0, 64, 8),
+                                          (24, 7.0, 20, 3), (8, 4.0, 8, 8)])
+def test_term_groups_parity(N, L, M, groups):
+    """Separated terms split over several clusters per cell (term_groups): same operator,
+    FP64 to 1e-12 and FP32 within its bound, collide and relax (Euler and Heun)."""
+    cells = 3
+    f = W.two_maxwellians(cells, N, L, seed=91)
+    og = oracle_grid(N, L, M)
+    Qref = O.collide(f, og)
+    with B.Grid(N, L, 1.0, M, term_groups=groups) as g:
+        assert rel_l2(run_collide(g, f, B.BOLTZ_FP64), Qref) <= 1e-12
+        assert rel_l2(run_collide(g, f, B.BOLTZ_FP32_FFT), Qref) <= fp32_tol(f, og)
+        for rk in (1, 2):
+            ref = O.relax(f, og, 0.004, 2, rk_order=rk)
+            ft = torch.from_numpy(f).cuda()
+            B.boltz_relax(g.batch(cells), ft, 0.004, 2, rk)
+            B.boltz_stream_status()
+            assert rel_l2(ft.cpu().numpy() - f, ref - f) <= 1e-11
+
+
+def test_term_groups_independent_of_batch_size_and_indexed():
+    """With a fixed term_groups the result of a cell does not depend on the batch around
+    it (bitwise), and indexed launches report bad indices in split mode too."""
+    N, L, M, pool = 16, 6.0, 16, 6
+    f = W.two_maxwellians(pool, N, L, seed=93)
+    with B.Grid(N, L, 1.0, M, term_groups=4) as g:
+        fd = torch.from_numpy(f).cuda()
+        Qall = torch.empty_like(fd)
+        B.boltz_collide(g.batch(pool), fd, Qall)
+        Q1 = torch.empty_like(fd[:1])
+        B.boltz_collide(g.batch(1), fd[4:5], Q1)
+        idx = torch.tensor([5, 1], dtype=torch.int64, device="cuda")
+        Qi = torch.zeros_like(fd)
+        B.boltz_collide_indexed(g.batch(2), fd, Qi, idx, pool)
+        B.boltz_stream_status()
+        assert torch.equal(Q1[0], Qall[4])
+        assert torch.equal(Qi[5], Qall[5]) and torch.equal(Qi[1], Qall[1])
+        bad = torch.tensor([2, pool], dtype=torch.int64, device="cuda")
+        Qb = torch.zeros_like(fd)
+        B.boltz_collide_indexed(g.batch(2), fd, Qb, bad, pool)
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_stream_status()
+        assert ei.value.status == 1  # BOLTZ_EINVAL
+        assert torch.equal(Qb[2], Qall[2])
