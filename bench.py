@@ -48,6 +48,11 @@ WORKLOADS = {
     # one cell, Maxwell molecules through the rank-16 radial expansion, 32 spherical-
     # Fibonacci directions, 3D BKW datum at K = 3/5 on the box of support radius 6,
     # one Heun step (two collision evaluations) per bench step
+    # ragged batch: 10000 cells, N in {16: 40 %, 24: 30 %, 32: 25 %, 48: 5 %}, M in {32, 64},
+    # gamma in {0, 0.5, 1} drawn per cell; one group (grid) per (N, M, gamma); 48^3 cells
+    # have no kernel in this build and are counted as rejected
+    "ragged": dict(cells=10000, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20164,
+                   ragged=True),
     "bkw16": dict(cells=1, N=16, L=(3.0 + math.sqrt(2.0)) * 3.0, M=32, gamma=0.0, dt=0.01, prec="fp64", f64=True,
                   seed=20161, rk=2, init="bkw",
                   opts=dict(dirs_kind=1, C_gamma=1.0 / (4.0 * math.pi), radial_rank=16, term_groups=64)),
@@ -74,10 +79,10 @@ NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA 
 NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor), nominal
 # DRAM bytes (read + write) per cell of one collide_kernel launch, from one ncu capture of
 # the current kernels on a smaller batch of the same workload (traffic grows with the
-# number of cells): profiles/collide_fp32_n32_2048cells.md (505.76 MB / 2048 cells) and
-# profiles/collide_fp64_n32_512cells.md (268.27 MB / 512 cells).  Must be re-taken (or set
-# to None) whenever the kernel changes.
-NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": 505.76e6 / 2048, "fp64": 268.27e6 / 512}
+# number of cells): profiles/collide_fp32_n32_2048cells.md and
+# profiles/collide_fp64_n32_512cells.md.  Must be re-taken (or set to None) whenever the
+# kernel changes.
+NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": None, "fp64": (173.19e6 + 94.70e6) / 512}
 
 
 def algorithmic_flops(N: int, M: int) -> float:
@@ -290,6 +295,117 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
             "term_groups": {str(k): v for k, v in term_groups.items()}}
 
 
+RAGGED_L = {16: 6.0, 24: 7.0, 32: 8.0, 48: 8.0}
+
+
+def ragged_groups(wl: dict):
+    """Seeded per-cell (N, M, gamma) of the ragged batch, grouped: {(N, M, gamma): cells}."""
+    rng = np.random.Generator(np.random.PCG64(wl["seed"]))
+    n = wl["cells"]
+    Ns = rng.choice([16, 24, 32, 48], size=n, p=[0.40, 0.30, 0.25, 0.05])
+    Ms = rng.choice([32, 64], size=n)
+    gs = rng.choice([0.0, 0.5, 1.0], size=n)
+    groups = {}
+    for N, M, g in zip(Ns.tolist(), Ms.tolist(), gs.tolist()):
+        groups[(N, M, g)] = groups.get((N, M, g), 0) + 1
+    return dict(sorted(groups.items()))
+
+
+def run_ragged(args, wl):
+    """Ragged batch through boltz_plan_*: per-shape launches (one boltz_relax per group,
+    no graph) against one graph launch per step (groups as concurrent branches), with and
+    without the autotuner.  value = cells of the supported groups x steps / time of the
+    autotuned plan."""
+    import torch
+
+    from paper_1608_08009_gb300 import boltz as B
+    from paper_1608_08009_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.lib()
+    spec = ragged_groups(wl)
+    rejected = sum(c for (N, _, _), c in spec.items() if N == 48)
+    grids, fs, f0s, info = [], [], [], []
+    for i, ((N, M, gamma), cells) in enumerate(spec.items()):
+        if N == 48:
+            continue
+        L = RAGGED_L[N]
+        g = B.Grid(N, L, gamma, M, C_gamma=1.0 / (4.0 * math.pi) if gamma == 0.0 else 1.0)
+        f = torch.from_numpy(W.two_maxwellians(cells, N, L, wl["seed"] + 1000 + i)).float().cuda()
+        grids.append(g)
+        fs.append(f)
+        f0s.append(f.clone())
+        info.append({"N": N, "M": M, "gamma": gamma, "cells": cells, "M_eff": g.info["M_eff"]})
+    cells_total = sum(x["cells"] for x in info)
+    flops = sum(algorithmic_flops(x["N"], x["M_eff"]) * x["cells"] for x in info)
+    stream = torch.cuda.current_stream()
+    dt = wl["dt"]
+
+    def reset():
+        for f, f0 in zip(fs, f0s):
+            f.copy_(f0)
+
+    def timed(step_fn):
+        reset()
+        for _ in range(args.warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        B.boltz_stream_status(stream)
+        return e0.elapsed_time(e1) / args.steps  # ms per step
+
+    def per_shape():
+        for g, f, x in zip(grids, fs, info):
+            B.boltz_relax(g.batch(x["cells"], B.BOLTZ_FP32_FFT, False), f, dt, 1, 1, stream)
+
+    ms_shape = timed(per_shape)
+    groups = [(g, f, B.BOLTZ_FP32_FFT) for g, f in zip(grids, fs)]
+    with B.Plan(groups, dt, 1, 1, 0, stream) as p:
+        ms_graph = timed(lambda: p.run(stream))
+    t_tune = time.perf_counter()
+    sampler = ClockSampler(local)
+    with B.Plan(groups, dt, 1, 1, B.BOLTZ_PLAN_AUTOTUNE, stream) as p:
+        tune_s = time.perf_counter() - t_tune
+        for i, x in enumerate(info):
+            x.update(p.info(i))
+        sampler.start()
+        time.sleep(0.3)
+        ms_tuned = timed(lambda: p.run(stream))
+        clocks = sampler.stop()
+    value = cells_total / (ms_tuned / 1000.0)
+    peak = NOMINAL_FP32_TFLOPS
+    line = {
+        "metric": "cell-collisions/s", "value": value, "unit": "cell-collisions/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_tuned, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ragged", "cells": wl["cells"], "cells_run": cells_total, "rejected_48cubed": rejected,
+                   "mix": "N 16/24/32/48: 40/30/25/5 %; M 32/64; gamma 0/0.5/1 (rank-16 expansion for gamma != 1)",
+                   "L_by_N": RAGGED_L, "dt": dt, "precision": "fp32_fft", "f_storage": "f32",
+                   "l2_policy": "inputs larger than L2 (f is %.2f GB)" % (sum(f.numel() * 4 for f in fs) / 1e9),
+                   "parallelism": "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": flops / (ms_tuned / 1000.0) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / (ms_tuned / 1000.0) / 1e12 / peak, "traffic": None,
+                     "kernel": "collide_kernel, one launch per group per step",
+                     "peak_source": "FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz"},
+        "ragged": {"per_shape_launches_ms": ms_shape, "graph_plan_ms": ms_graph, "autotuned_graph_plan_ms": ms_tuned,
+                   "autotune_seconds": tune_s, "groups": info},
+        "gpu_launches": len(info) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for g in grids:
+        g.close()
+    return 0
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -332,6 +448,8 @@ def config_of(args, wl):
         extra["integrator"] = "Heun (2 collision evaluations per step)"
     if o.get("term_groups", 1) > 1:
         extra["term_groups"] = o["term_groups"]
+    if o.get("cluster_size"):
+        extra["cluster_size"] = o["cluster_size"]
     if wl.get("init") == "bkw":
         extra["datum"] = "3D BKW at K = 3/5, Maxwell molecules, B = 1/(4 pi), radial rank %d" % o.get("radial_rank", 16)
     return {"workload": args.workload, "cells_per_gpu": wl["cells"], "N_v": wl["N"], "L": wl["L"], "M_dirs": wl["M"],
@@ -540,16 +658,21 @@ def main():
     ap.add_argument("--serve-groups", type=str, default="",
                     help="term groups of the serving grids, e.g. 16:4,32:8 (default)")
     ap.add_argument("--term-groups", type=int, default=0, help="override the workload grid's term_groups")
+    ap.add_argument("--cluster-size", type=int, default=0, help="override the float32 cluster size")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.cells > 0:
         wl["cells"] = args.cells
     if args.term_groups > 0:
         wl["opts"] = dict(wl.get("opts", {}), term_groups=args.term_groups)
+    if args.cluster_size > 0:
+        wl["opts"] = dict(wl.get("opts", {}), cluster_size=args.cluster_size)
     args.serve_groups = ({int(a): int(b) for a, b in (kv.split(":") for kv in args.serve_groups.split(","))}
                          if args.serve_groups else None)
     if args.impl == "reference":
         return run_reference(args, wl)
+    if wl.get("ragged"):
+        return run_ragged(args, wl)
     return run_ours(args, wl)
 
 

@@ -87,6 +87,14 @@ typedef struct {
                         of (G + 1) N^3 values per cell (grown on demand, kept with the
                         grid).  Clamped to [1, M_eff].  Results depend on G (rounding
                         order of the gain sum) but not on the batch size.               */
+  int cluster_size;  /* thread-block cluster size (CTAs per cell) of the float32 path;
+                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 8).  Also built:
+                        16: 2, 4; 24: 2, 6; 32: 4, 16.  Larger clusters give each CTA
+                        a thinner slab (fewer threads, more CTAs per SM).  The float64
+                        path always uses its own size (8: 1, 16: 2, 24: 3, 32: 8).
+                        Results agree across sizes up to the rounding of the moment sums
+                        (summed per CTA, then across the cluster).  Other values:
+                        BOLTZ_EUNSUPPORTED. */
 } boltz_grid_opts;
 
 typedef struct boltz_grid_s* boltz_grid;
@@ -171,6 +179,46 @@ boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, double dt, int s
  * on one grid must not overlap.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
 boltz_status boltz_relax_host(const boltz_batch* b, const void* f_in, void* f_out, double dt, int steps,
                               int rk_order, int64_t chunk_cells, void* stream);
+
+/* ---- Ragged batches ------------------------------------------------------------------
+ * A plan advances several groups of cells, each group on its own grid (any mix of N_v,
+ * M_dirs, gamma, precision), by `steps` Euler (rk_order 1) or Heun (rk_order 2) steps of
+ * the relaxation of Sec. 3.1 (Eq. relax, Eq. f_coll) per boltz_plan_run, projecting onto
+ * the moments each cell had when the run started (as boltz_relax).  The kernels are
+ * specialised per N, so a step is one launch per group; the plan captures the whole step
+ * loop as one CUDA graph in which every group is a concurrent branch, and
+ * boltz_plan_run launches that graph on `stream`.
+ * Autotuning (BOLTZ_PLAN_AUTOTUNE) times, for every group, each candidate (term groups,
+ * cluster size) on a copy of the group's cells at plan creation and keeps the fastest;
+ * without it a group uses its grid's term_groups and the default cluster size, and the
+ * results equal boltz_relax's bit for bit.  BOLTZ_PLAN_SERIAL puts the groups one after
+ * another on one branch (for comparison).
+ * Ownership: the caller owns the grids and the device arrays f, which must stay valid and
+ * in place for the plan's life; each group's grid must be distinct and must not be used
+ * by other calls while the plan runs (its scratch is shared).  The plan owns its
+ * streams, scratch (targets, Heun stage) and graph.  boltz_plan_create synchronises
+ * `stream` and the device.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+typedef struct boltz_plan_s* boltz_plan;
+
+typedef struct {
+  boltz_grid grid;
+  int64_t n_cells;   /* cells of this group, >= 0                                       */
+  int prec;          /* a boltz_precision                                               */
+  int f_is_fp64;     /* 1: f is float64; 0: float32                                     */
+  void* f;           /* device array [n_cells][N^3], advanced in place by each run      */
+} boltz_group;
+
+enum { BOLTZ_PLAN_AUTOTUNE = 1, BOLTZ_PLAN_SERIAL = 2 };
+
+boltz_status boltz_plan_create(const boltz_group* groups, int n_groups, double dt, int steps, int rk_order,
+                               int flags, void* stream, boltz_plan* out);
+/* One graph launch: every group advances by the plan's steps.  Asynchronous on stream. */
+boltz_status boltz_plan_run(boltz_plan p, void* stream);
+/* The launch configuration chosen for group `group`: term groups, cluster size and the
+ * tuned duration of one launch in microseconds (0 when not tuned).  Outputs nullable. */
+boltz_status boltz_plan_group_info(boltz_plan p, int group, int* term_groups, int* cluster, double* tuned_us);
+/* Synchronises the device, frees the plan.  NULL is a no-op. */
+boltz_status boltz_plan_destroy(boltz_plan p);
 
 /* Cells addressed through an index array (ragged batches, resident pools): cell c of the
  * call is slot cell_idx[c] of f (and of Q), with slot s at offset s * N^3.  cell_idx is a

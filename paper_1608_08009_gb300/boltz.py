@@ -35,7 +35,8 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_relax", "boltz_moments", "boltz_stream_status", "boltz_last_error",
             "boltz_grid_info", "boltz_grid_tables", "boltz_version", "boltz_relax_noalloc",
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
-            "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host")
+            "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
+            "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy")
 
 
 class BoltzError(RuntimeError):
@@ -47,13 +48,21 @@ class BoltzError(RuntimeError):
 class boltz_grid_opts(ctypes.Structure):
     _fields_ = [("dirs_kind", ctypes.c_int), ("dirs_a1", ctypes.c_int), ("R_trunc", ctypes.c_double),
                 ("C_gamma", ctypes.c_double), ("radial_rank", ctypes.c_int), ("inner_nodes", ctypes.c_int),
-                ("project", ctypes.c_int), ("term_groups", ctypes.c_int)]
+                ("project", ctypes.c_int), ("term_groups", ctypes.c_int), ("cluster_size", ctypes.c_int)]
 
 
 class boltz_batch(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_void_p), ("n_cells", ctypes.c_int64), ("prec", ctypes.c_int),
                 ("f_is_fp64", ctypes.c_int)]
 
+
+class boltz_group(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("n_cells", ctypes.c_int64), ("prec", ctypes.c_int),
+                ("f_is_fp64", ctypes.c_int), ("f", ctypes.c_void_p)]
+
+
+BOLTZ_PLAN_AUTOTUNE = 1
+BOLTZ_PLAN_SERIAL = 2
 
 _lib = None
 
@@ -76,6 +85,10 @@ def lib() -> ctypes.CDLL:
         L.boltz_moments.argtypes = [P(boltz_batch), vp, vp, vp]
         L.boltz_relax_noalloc.argtypes = [P(boltz_batch), vp, f64, i32, vp]
         L.boltz_relax_host.argtypes = [P(boltz_batch), vp, vp, f64, i32, i32, i64, vp]
+        L.boltz_plan_create.argtypes = [P(boltz_group), i32, f64, i32, i32, i32, vp, P(vp)]
+        L.boltz_plan_run.argtypes = [vp, vp]
+        L.boltz_plan_group_info.argtypes = [vp, i32, P(i32), P(i32), P(f64)]
+        L.boltz_plan_destroy.argtypes = [vp]
         L.boltz_collide_indexed.argtypes = [P(boltz_batch), vp, vp, vp, i64, vp]
         L.boltz_relax_indexed.argtypes = [P(boltz_batch), vp, vp, i64, f64, i32, vp]
         L.boltz_server_create.argtypes = [P(vp), i32, i32, f64, ctypes.c_size_t, vp, P(vp)]
@@ -94,7 +107,8 @@ def lib() -> ctypes.CDLL:
                      "boltz_moments", "boltz_stream_status", "boltz_grid_info", "boltz_grid_tables",
                      "boltz_relax_noalloc", "boltz_collide_indexed", "boltz_relax_indexed",
                      "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
-                     "boltz_server_destroy", "boltz_relax_host"):
+                     "boltz_server_destroy", "boltz_relax_host", "boltz_plan_create", "boltz_plan_run",
+                     "boltz_plan_group_info", "boltz_plan_destroy"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -278,6 +292,49 @@ class Grid:
     def close(self) -> None:
         if getattr(self, "handle", None):
             boltz_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Plan:
+    """Owning handle of a ragged-batch plan.  `groups`: list of (Grid, f tensor, prec);
+    the tensors must stay alive and in place while the plan exists."""
+
+    def __init__(self, groups, dt: float, steps: int, rk_order: int = 1, flags: int = 0, stream=None):
+        arr = (boltz_group * len(groups))()
+        self._keep = []
+        for i, (grid, f, prec) in enumerate(groups):
+            fp64 = str(f.dtype) == "torch.float64"
+            arr[i] = boltz_group(grid.handle, f.shape[0], prec, 1 if fp64 else 0, _ptr(f))
+            self._keep.append(f)
+        h = ctypes.c_void_p()
+        _check(lib().boltz_plan_create(arr, len(groups), dt, steps, rk_order, flags, _stream(stream),
+                                       ctypes.byref(h)))
+        self.handle = h.value
+        self.n_groups = len(groups)
+
+    def run(self, stream=None) -> None:
+        _check(lib().boltz_plan_run(self.handle, _stream(stream)))
+
+    def info(self, group: int) -> dict:
+        G, C, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().boltz_plan_group_info(self.handle, group, ctypes.byref(G), ctypes.byref(C), ctypes.byref(us)))
+        return {"term_groups": G.value, "cluster": C.value, "tuned_us": us.value}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().boltz_plan_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

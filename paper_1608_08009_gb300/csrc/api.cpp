@@ -80,6 +80,7 @@ void boltz_default_opts(boltz_grid_opts* o) {
   o->radial_rank = 0;
   o->inner_nodes = 128;
   o->term_groups = 1;
+  o->cluster_size = 0;
   o->project = 1;
 }
 
@@ -130,6 +131,16 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
     set_error("term_groups must lie in [0, 4096]");
     return BOLTZ_EINVAL;
   }
+  if (o.cluster_size != 0) {
+    int cl[4];
+    const int k = boltz::cluster_choices(N_v, BOLTZ_FP32_FFT, cl);
+    bool ok = false;
+    for (int i = 0; i < k; ++i) ok |= (cl[i] == o.cluster_size);
+    if (!ok) {
+      set_error("no float32 kernel with this cluster size for this N");
+      return BOLTZ_EUNSUPPORTED;
+    }
+  }
   boltz_grid_s* g = new (std::nothrow) boltz_grid_s();
   if (!g) {
     set_error("out of host memory");
@@ -152,6 +163,7 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
   g->inner_nodes = o.inner_nodes;
   g->project = o.project ? 1 : 0;
   g->term_groups = std::max(1, std::min(o.term_groups, M_dirs * rank));
+  g->cluster_size = o.cluster_size;
   g->R = o.R_trunc > 0 ? o.R_trunc : 0.0;
   boltz_status st = boltz::build_tables(g);
   if (st == BOLTZ_OK) st = boltz::upload_tables(g);
@@ -337,19 +349,23 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
 namespace boltz {
 
 boltz_status relax_steps(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, void* f, double dt,
-                         int steps, int rk_order, cudaStream_t s, double* U0, void* stage) {
+                         int steps, int rk_order, cudaStream_t s, double* U0, void* stage, int groups,
+                         int cluster) {
   boltz_status st;
   // Targets: Phi-sums of the initial state (Eq. minim1 with U fixed), computed by the
   // first launch from the values it loads anyway and kept in U0 for the later ones.
   for (int it = 0; it < steps; ++it) {
     const int first = (it == 0) ? 1 : 0;
     if (rk_order == 1) {
-      st = launch_collide(g, n_cells, prec, f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, U0, first, 1, s);
+      st = launch_collide(g, n_cells, prec, f_is_fp64, f, nullptr, f, 0.0, 1.0, dt, U0, first, 1, s, nullptr, 0,
+                          groups, cluster);
       if (st != BOLTZ_OK) return st;
     } else {
-      st = launch_collide(g, n_cells, prec, f_is_fp64, f, nullptr, stage, 0.0, 1.0, dt, U0, first, 1, s);
+      st = launch_collide(g, n_cells, prec, f_is_fp64, f, nullptr, stage, 0.0, 1.0, dt, U0, first, 1, s, nullptr,
+                          0, groups, cluster);
       if (st != BOLTZ_OK) return st;
-      st = launch_collide(g, n_cells, prec, f_is_fp64, stage, f, f, 0.5, 0.5, 0.5 * dt, U0, 0, 1, s);
+      st = launch_collide(g, n_cells, prec, f_is_fp64, stage, f, f, 0.5, 0.5, 0.5 * dt, U0, 0, 1, s, nullptr, 0,
+                          groups, cluster);
       if (st != BOLTZ_OK) return st;
     }
   }

@@ -24,6 +24,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 
@@ -80,6 +81,10 @@ struct CollideCfg {
   static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
   static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
   static constexpr int WARPS = THREADS / 32;
+  // CTAs per SM asked of the register allocator.  float32 32^3 with C = 8: 3 (168
+  // registers, 44 bytes spilled outside the term loop) runs 11 % faster on GB300 than the
+  // 252-register 2-CTA version: twelve warps hide the table loads and barrier waits.
+  static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && N == 32 && C == 8) ? 3 : 1;
   using T2 = typename Vec2<T>::type;
   static constexpr bool kF32 = sizeof(T) == 4;
   // float32: the spectrum pencil of each thread stays in registers and the x-plane
@@ -179,7 +184,7 @@ __device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, dou
 }
 
 template <typename T, typename TIO, int N, int C, bool kSplit>
-__global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, 1)
+__global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, CollideCfg<T, N, C>::MIN_BLOCKS)
 collide_kernel(const CollideArgs args) {
   using Cfg = CollideCfg<T, N, C>;
   using T2 = typename Cfg::T2;
@@ -653,12 +658,44 @@ boltz_status upload_tables(boltz_grid_s* g) {
 template <typename T, typename TIO, int N, int C>
 static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
   using Cfg = CollideCfg<T, N, C>;
-  auto kern = (a.groups > 1) ? collide_kernel<T, TIO, N, C, true> : collide_kernel<T, TIO, N, C, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  if (C > 1) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const bool split = a.groups > 1;
+  auto kern = split ? collide_kernel<T, TIO, N, C, true> : collide_kernel<T, TIO, N, C, false>;
+  // function attributes are per device: set them once per (instantiation, device), and
+  // check once that a cluster of this size can be scheduled at all
+  static std::atomic<unsigned long long> prepared[2], unschedulable[2];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    if (C > 1) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(C, 1, 1);
+      q.blockDim = dim3(Cfg::THREADS, 1, 1);
+      q.dynamicSmemBytes = Cfg::SMEM;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = C;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int clusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&clusters, kern, &q);
+      if (e != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        if (dev < 64) unschedulable[split].fetch_or(bit, std::memory_order_release);
+      }
+    }
+    if (dev < 64) prepared[split].fetch_or(bit, std::memory_order_release);
+  }
+  if (dev < 64 && (unschedulable[split].load(std::memory_order_acquire) & bit)) {
+    set_error("a thread-block cluster of this size cannot be scheduled on this device");
+    return BOLTZ_EUNSUPPORTED;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
@@ -681,55 +718,114 @@ bool collide_supported(int N, int prec) {
   return (N == 8 || N == 16 || N == 24 || N == 32) && (prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT);
 }
 
+// Cluster sizes.  float64: the smallest C whose per-CTA slab fits shared memory and
+// registers.  float32: measured on GB300 -- at 32^3, C = 8 (128-thread CTAs, two clusters
+// per SM whose barrier waits overlap) beats C = 4 (one 256-thread CTA per SM) by 8 % and
+// C = 16 by 30 %; at 24^3 the autotuner prefers 3 to 2.  The other built sizes are
+// candidates for the autotuner of ragged plans and for boltz_grid_opts.cluster_size.
+int default_cluster(int N, int prec) {
+  const bool dbl = (prec == BOLTZ_FP64);
+  switch (N) {
+    case 8: return 1;
+    case 16: return dbl ? 2 : 1;
+    case 24: return 3;
+    case 32: return 8;
+    default: return 0;
+  }
+}
+
+int cluster_choices(int N, int prec, int* out) {
+  int k = 0;
+  out[k++] = default_cluster(N, prec);
+  if (prec != BOLTZ_FP64) {
+    if (N == 16) {
+      out[k++] = 2;
+      out[k++] = 4;
+    }
+    if (N == 24) {
+      out[k++] = 2;
+      out[k++] = 6;
+    }
+    if (N == 32) {
+      out[k++] = 4;
+      out[k++] = 16;
+    }
+  }
+  return k;
+}
+
 template <typename T, typename TIO>
-static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
-  // cluster sizes: the smallest C whose per-CTA slab fits shared memory and registers
+static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
+                               int cluster) {
   constexpr bool dbl = sizeof(T) == 8;
-  if (g->N == 8) return launch_impl<T, TIO, 8, 1>(a, n_cells, st);
-  if (g->N == 16) return launch_impl<T, TIO, 16, dbl ? 2 : 1>(a, n_cells, st);
-  if (g->N == 24) return launch_impl<T, TIO, 24, dbl ? 3 : 2>(a, n_cells, st);
-  if (g->N == 32) return launch_impl<T, TIO, 32, dbl ? 8 : 4>(a, n_cells, st);
-  set_error("no collision kernel for this N");
+  const int C = cluster > 0 ? cluster : default_cluster(g->N, dbl ? BOLTZ_FP64 : BOLTZ_FP32_FFT);
+  if (g->N == 8 && C == 1) return launch_impl<T, TIO, 8, 1>(a, n_cells, st);
+  if constexpr (dbl) {
+    if (g->N == 16 && C == 2) return launch_impl<T, TIO, 16, 2>(a, n_cells, st);
+    if (g->N == 24 && C == 3) return launch_impl<T, TIO, 24, 3>(a, n_cells, st);
+    if (g->N == 32 && C == 8) return launch_impl<T, TIO, 32, 8>(a, n_cells, st);
+  } else {
+    if (g->N == 16 && C == 1) return launch_impl<T, TIO, 16, 1>(a, n_cells, st);
+    if (g->N == 16 && C == 2) return launch_impl<T, TIO, 16, 2>(a, n_cells, st);
+    if (g->N == 16 && C == 4) return launch_impl<T, TIO, 16, 4>(a, n_cells, st);
+    if (g->N == 24 && C == 2) return launch_impl<T, TIO, 24, 2>(a, n_cells, st);
+    if (g->N == 24 && C == 3) return launch_impl<T, TIO, 24, 3>(a, n_cells, st);
+    if (g->N == 24 && C == 6) return launch_impl<T, TIO, 24, 6>(a, n_cells, st);
+    if (g->N == 32 && C == 4) return launch_impl<T, TIO, 32, 4>(a, n_cells, st);
+    if (g->N == 32 && C == 8) return launch_impl<T, TIO, 32, 8>(a, n_cells, st);
+    if (g->N == 32 && C == 16) return launch_impl<T, TIO, 32, 16>(a, n_cells, st);
+  }
+  set_error("no collision kernel for this (N, precision, cluster size)");
   return BOLTZ_EUNSUPPORTED;
+}
+
+// Scratch of split launches: [cells] arrival counters (zeroed once; every launch leaves
+// them at zero), then the partial gains [cells][G][n] and the loss multipliers [cells][n].
+boltz_status ensure_split_scratch(const boltz_grid_s* g, int64_t n_cells, int G, int prec, cudaStream_t stream) {
+  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t tsz = (prec == BOLTZ_FP64) ? sizeof(double) : sizeof(float);
+  const size_t cnt_bytes = ((size_t)n_cells * sizeof(unsigned) + 255) / 256 * 256;
+  const size_t need = cnt_bytes + (size_t)n_cells * (G + 1) * n * tsz;
+  if (need <= g->split_cap) return BOLTZ_OK;
+  // the old buffer may still be read by work queued on this stream
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "split scratch sync");
+  cudaFree(g->split_buf);
+  g->split_buf = nullptr;
+  g->split_cap = 0;
+  if (cudaMalloc(&g->split_buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("split scratch allocation failed");
+    return BOLTZ_ENOMEM;
+  }
+  if ((e = cudaMemset(g->split_buf, 0, need)) != cudaSuccess) return cuda_fail(e, "split scratch clear");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "split scratch clear");
+  g->split_cap = need;
+  return BOLTZ_OK;
 }
 
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, const void* f_in,
                             const void* f_base, void* out, double a, double b, double s, double* Utgt,
                             int compute_targets, int project, cudaStream_t stream, const int64_t* cell_idx,
-                            int64_t pool_cells, int groups) {
+                            int64_t pool_cells, int groups, int cluster) {
   if (n_cells == 0) return BOLTZ_OK;
   if (!collide_supported(g->N, prec)) {
     set_error("unsupported (N, precision) combination");
     return BOLTZ_EUNSUPPORTED;
   }
+  if (cluster == 0 && prec != BOLTZ_FP64) cluster = g->cluster_size;  // 0: the default of (N, prec)
   int G = groups < 0 ? g->term_groups : groups;
   G = std::max(1, std::min(G, g->M_eff));
-  if (n_cells * (int64_t)G * 8 > (int64_t)INT32_MAX) {
+  if (n_cells * (int64_t)G * 16 > (int64_t)INT32_MAX) {
     set_error("n_cells * term_groups too large for one launch");
     return BOLTZ_EINVAL;
   }
   const size_t n = (size_t)g->N * g->N * g->N;
   const size_t tsz = (prec == BOLTZ_FP64) ? sizeof(double) : sizeof(float);
-  // scratch of split launches: [cells] arrival counters (zeroed once; each launch leaves
-  // them at zero), then the partial gains and the loss multipliers
   const size_t cnt_bytes = ((size_t)n_cells * sizeof(unsigned) + 255) / 256 * 256;
   if (G > 1) {
-    const size_t need = cnt_bytes + (size_t)n_cells * (G + 1) * n * tsz;
-    if (need > g->split_cap) {
-      // the old buffer may still be read by work queued on this stream
-      cudaError_t e = cudaStreamSynchronize(stream);
-      if (e != cudaSuccess) return cuda_fail(e, "split scratch sync");
-      cudaFree(g->split_buf);
-      g->split_buf = nullptr;
-      g->split_cap = 0;
-      if (cudaMalloc(&g->split_buf, need) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("split scratch allocation failed");
-        return BOLTZ_ENOMEM;
-      }
-      if ((e = cudaMemset(g->split_buf, 0, need)) != cudaSuccess) return cuda_fail(e, "split scratch clear");
-      g->split_cap = need;
-    }
+    boltz_status r = ensure_split_scratch(g, n_cells, G, prec, stream);
+    if (r != BOLTZ_OK) return r;
   }
   CollideArgs args;
   args.f_in = f_in;
@@ -755,12 +851,12 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.loss = (G > 1) ? sb + cnt_bytes + (size_t)n_cells * G * n * tsz : nullptr;
   if (prec == BOLTZ_FP64) {
     args.tab = g->tab64;
-    return f_is_fp64 ? dispatch_n<double, double>(g, args, n_cells, stream)
-                     : dispatch_n<double, float>(g, args, n_cells, stream);
+    return f_is_fp64 ? dispatch_n<double, double>(g, args, n_cells, stream, cluster)
+                     : dispatch_n<double, float>(g, args, n_cells, stream, cluster);
   }
   args.tab = g->tab32;
-  return f_is_fp64 ? dispatch_n<float, double>(g, args, n_cells, stream)
-                   : dispatch_n<float, float>(g, args, n_cells, stream);
+  return f_is_fp64 ? dispatch_n<float, double>(g, args, n_cells, stream, cluster)
+                   : dispatch_n<float, float>(g, args, n_cells, stream, cluster);
 }
 
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f, double* U,

@@ -32,6 +32,7 @@ struct boltz_grid_s {
   int M = 0, rank = 1, M_eff = 0;
   int dirs_kind = 0, a1 = 0, inner_nodes = 128, project = 1;
   int term_groups = 1;  // clusters per cell sharing its separated terms (1 = no split)
+  int cluster_size = 0; // cluster size of the float32 path (0 = default)
   int device = 0;
   // float64 host tables, mode storage order (kx, ky, kz), kz fastest
   std::vector<double> e, wdir, w, alpha, alphap, D;
@@ -78,14 +79,22 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                             const void* f_in, const void* f_base, void* out, double a, double b,
                             double s, double* Utgt, int compute_targets, int project,
                             cudaStream_t stream, const int64_t* cell_idx = nullptr,
-                            int64_t pool_cells = 0, int groups = -1);  // groups < 0: the grid's term_groups
+                            int64_t pool_cells = 0, int groups = -1, int cluster = 0);
+// groups < 0: the grid's term_groups; cluster 0: the default cluster size of (N, prec)
+int default_cluster(int N, int prec);
+// Grow the grid's scratch of split launches (term groups) to n_cells cells of G groups;
+// synchronises `stream` when it has to reallocate.
+boltz_status ensure_split_scratch(const boltz_grid_s* g, int64_t n_cells, int G, int prec, cudaStream_t stream);
+// Cluster sizes with a kernel for (N, prec), the default first; returns the count (<= 4).
+int cluster_choices(int N, int prec, int* out);
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
                             double* U, double scale, cudaStream_t stream);
 bool collide_supported(int N, int prec);
 // `steps` Euler or Heun steps of n_cells cells of f in place (the body of boltz_relax);
 // U0: [n_cells][5] scratch for the targets, stage: one copy of f (Heun only).
 boltz_status relax_steps(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, void* f, double dt,
-                         int steps, int rk_order, cudaStream_t s, double* U0, void* stage);
+                         int steps, int rk_order, cudaStream_t s, double* U0, void* stage, int groups = -1,
+                         int cluster = 0);
 void free_host_pipeline(boltz_grid_s* g);
 // Argument checks shared by the entry points (api.cpp): set the error message on failure.
 boltz_status check_batch(const boltz_batch* b);
