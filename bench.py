@@ -49,8 +49,7 @@ WORKLOADS = {
     # Fibonacci directions, 3D BKW datum at K = 3/5 on the box of support radius 6,
     # one Heun step (two collision evaluations) per bench step
     # ragged batch: 10000 cells, N in {16: 40 %, 24: 30 %, 32: 25 %, 48: 5 %}, M in {32, 64},
-    # gamma in {0, 0.5, 1} drawn per cell; one group (grid) per (N, M, gamma); 48^3 cells
-    # have no kernel in this build and are counted as rejected
+    # gamma in {0, 0.5, 1} drawn per cell; one group (grid) per (N, M, gamma)
     "ragged": dict(cells=10000, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20164,
                    ragged=True),
     "bkw16": dict(cells=1, N=16, L=(3.0 + math.sqrt(2.0)) * 3.0, M=32, gamma=0.0, dt=0.01, prec="fp64", f64=True,
@@ -206,27 +205,27 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     """Serving load (continuous batching through boltz_server_*): Poisson arrivals at
     `rate` req/s for `seconds`; each request is one cell relaxing for U{10..200} forward
     Euler steps, N in {16 (60 %), 32 (35 %), 64 (5 %)}, gamma = 1, M = 64, dt = 0.0025,
-    float32 path, admission by an HBM budget.  64^3 requests are rejected (no kernel for
-    that size in this build).  Latency = completion seen by the host - arrival."""
+    float32 path, admission by an HBM budget.  Latency = completion seen by the host -
+    arrival."""
     import torch
 
     from paper_1608_08009_gb300 import boltz as B
     from paper_1608_08009_gb300 import workloads as W
 
-    term_groups = term_groups or {16: 4, 32: 8}
+    term_groups = term_groups or {16: 4, 32: 8, 64: 4}
     rng = np.random.Generator(np.random.PCG64(seed))
     n_req = int(rng.poisson(rate * seconds))
     arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
     sizes = rng.choice([16, 32, 64], size=n_req, p=[0.60, 0.35, 0.05])
     steps = rng.integers(10, 201, size=n_req)
-    # 16^3 jobs on [-6, 6)^3 (dv = 0.75), 32^3 jobs on [-8, 8)^3 (dv = 0.5)
-    Ls = {16: 6.0, 32: 8.0}
+    # 16^3 jobs on [-6, 6)^3 (dv = 0.75), 32^3 and 64^3 jobs on [-8, 8)^3 (dv = 0.5, 0.25)
+    Ls = {16: 6.0, 32: 8.0, 64: 8.0}
     # term groups: a job's separated terms spread over several clusters, fixed per grid so
     # a job's arithmetic does not depend on what else is resident
-    grids = {N: B.Grid(N, Ls[N], 1.0, 64, term_groups=term_groups[N]) for N in (16, 32)}
-    gidx = {16: 0, 32: 1}
+    grids = {N: B.Grid(N, Ls[N], 1.0, 64, term_groups=term_groups[N]) for N in (16, 32, 64)}
+    gidx = {16: 0, 32: 1, 64: 2}
     stream = torch.cuda.current_stream()
-    server = B.Server([grids[16], grids[32]], B.BOLTZ_FP32_FFT, 0.0025, budget_bytes, stream)
+    server = B.Server([grids[16], grids[32], grids[64]], B.BOLTZ_FP32_FFT, 0.0025, budget_bytes, stream)
     reqs = []
     for k in range(n_req):
         N = int(sizes[k])
@@ -236,7 +235,7 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
         f = W.two_maxwellians(n_req, N, Ls[N], seed, cells=[k])[0].astype(np.float32).ravel()
         reqs.append((torch.from_numpy(f).pin_memory(), torch.empty(f.size, dtype=torch.float32).pin_memory()))
     # warm-up of both grids outside the measured window
-    for N in (16, 32):
+    for N in (16, 32, 64):
         f = torch.zeros(N ** 3, dtype=torch.float32).pin_memory() + 1e-3
         o = torch.empty_like(f)
         j = server.submit(gidx[N], f, o, 2)
@@ -277,6 +276,12 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     wall = time.perf_counter() - t0
     B.boltz_stream_status(stream)
     lat = np.array([done_t[k] - arrivals[k] for k in range(n_req) if done_t[k] is not None])
+    by_n = {}
+    for N in (16, 32, 64):
+        ln = np.array([done_t[k] - arrivals[k] for k in range(n_req) if done_t[k] is not None and sizes[k] == N])
+        if ln.size:
+            by_n[str(N)] = {"jobs": int(ln.size), "p50_s": float(np.percentile(ln, 50)),
+                            "p99_s": float(np.percentile(ln, 99))}
     served = [k for k in range(n_req) if done_t[k] is not None]
     cell_steps = int(sum(int(steps[k]) for k in served))
     server.close()
@@ -285,12 +290,12 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     return {"p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
             "mean_latency_s": float(lat.mean()) if lat.size else None,
-            "completed": len(served), "rejected_64cubed": int(np.sum(sizes == 64)),
+            "completed": len(served), "by_size": by_n,
             "unfinished": int(sum(1 for k in range(n_req) if reqs[k] is not None and done_t[k] is None)),
             "offered_req_per_s": rate, "arrival_window_s": seconds, "wall_s": wall,
             "cell_collisions_per_s": cell_steps / wall, "server_iterations": n_steps,
             "max_resident": max_res, "max_queued": max_q, "hbm_budget_bytes": budget_bytes,
-            "mix": "N=16 (L=6): 60 %, N=32 (L=8): 35 %, N=64: 5 % (rejected); steps U{10..200}; M=64; "
+            "mix": "N=16 (L=6): 60 %, N=32 (L=8): 35 %, N=64 (L=8): 5 %; steps U{10..200}; M=64; "
                    "gamma=1; dt=0.0025; f32",
             "term_groups": {str(k): v for k, v in term_groups.items()}}
 
@@ -325,11 +330,8 @@ def run_ragged(args, wl):
     torch.cuda.set_device(local)
     B.lib()
     spec = ragged_groups(wl)
-    rejected = sum(c for (N, _, _), c in spec.items() if N == 48)
     grids, fs, f0s, info = [], [], [], []
     for i, ((N, M, gamma), cells) in enumerate(spec.items()):
-        if N == 48:
-            continue
         L = RAGGED_L[N]
         g = B.Grid(N, L, gamma, M, C_gamma=1.0 / (4.0 * math.pi) if gamma == 0.0 else 1.0)
         f = torch.from_numpy(W.two_maxwellians(cells, N, L, wl["seed"] + 1000 + i)).float().cuda()
@@ -386,7 +388,7 @@ def run_ragged(args, wl):
         "metric": "cell-collisions/s", "value": value, "unit": "cell-collisions/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_tuned, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "ragged", "cells": wl["cells"], "cells_run": cells_total, "rejected_48cubed": rejected,
+        "config": {"workload": "ragged", "cells": wl["cells"], "cells_run": cells_total,
                    "mix": "N 16/24/32/48: 40/30/25/5 %; M 32/64; gamma 0/0.5/1 (rank-16 expansion for gamma != 1)",
                    "L_by_N": RAGGED_L, "dt": dt, "precision": "fp32_fft", "f_storage": "f32",
                    "l2_policy": "inputs larger than L2 (f is %.2f GB)" % (sum(f.numel() * 4 for f in fs) / 1e9),

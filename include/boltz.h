@@ -117,8 +117,10 @@ void boltz_default_opts(boltz_grid_opts* opts);
  * separable in 3D and a rank-r radial expansion is tabulated instead (r terms per
  * direction).  Builds the tables on the host in float64 and copies them to the
  * current device.
- *   N_v     points per axis; supported: 8, 16, 24, 32 (48 and 64 return
- *           BOLTZ_EUNSUPPORTED: their register pencils do not fit this kernel design).
+ *   N_v     points per axis: 8, 16, 24, 32 (float64 and float32 paths) and 48, 64
+ *           (float32 path only: a float64 pencil of 48 or 64 values does not fit one
+ *           thread's registers; float64 batches on these grids return
+ *           BOLTZ_EUNSUPPORTED).  Other even sizes: BOLTZ_EUNSUPPORTED.
  *   L       half-width of the velocity box [-L, L)^3, > 0.
  *   gamma   VHS exponent in [-3, 1] (1 = hard spheres, 0 = Maxwell molecules).
  *   M_dirs  number of directions, 1..4096.

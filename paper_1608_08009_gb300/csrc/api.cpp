@@ -90,8 +90,8 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
     set_error("null output handle");
     return BOLTZ_EINVAL;
   }
-  if (N_v != 8 && N_v != 16 && N_v != 24 && N_v != 32) {
-    set_error("N_v must be 8, 16, 24 or 32 in this build");
+  if (N_v != 8 && N_v != 16 && N_v != 24 && N_v != 32 && N_v != 48 && N_v != 64) {
+    set_error("N_v must be 8, 16, 24, 32, 48 or 64 in this build");
     return (N_v > 0 && N_v % 2 == 0) ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
   }
   if (!(L > 0) || !std::isfinite(L)) {
@@ -187,6 +187,7 @@ boltz_status boltz_destroy_grid(boltz_grid g) {
   cudaFree(g->U0);
   cudaFree(g->stage);
   cudaFree(g->split_buf);
+  cudaFree(g->spec_buf);
   boltz::free_host_pipeline(g);
   if (prev >= 0) cudaSetDevice(prev);
   delete g;

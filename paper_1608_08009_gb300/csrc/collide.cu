@@ -69,6 +69,7 @@ struct CollideArgs {
   void* part;          // [cells][G][n] T
   void* loss;          // [cells][n] T
   unsigned* arrivals;  // [cells], zero between launches
+  void* spec;          // N = 48, 64: spectrum pencils [cells][G][ky][kx][kz] float2
   KernelGeom geom;
 };
 
@@ -181,6 +182,63 @@ __device__ __forceinline__ void ld_local_chunk(const float2* p, float* re, float
 __device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, double* im) {
   const double2 v = *p;
   re[0] = v.x; im[0] = v.y;
+}
+
+// Projection of Sec. 3.2 (Eq. minim1) for one cell owned by a cluster: m[5] is this
+// thread's share of Phi g; red holds [WARPS][5] scratch, then [5] Phi g and [5] Phi f_in
+// (the targets, when computed) of this CTA.  Returns c5 = G (U - Phi g), zero without
+// projection; U is Phi f_in (compute_targets), Utgt[cell] or zero.  Ends with a cluster
+// barrier, after which no CTA reads a peer's shared memory.
+template <int C, int WARPS>
+__device__ __forceinline__ void cluster_correction(const CollideArgs& args, const double (&m)[5], double* red,
+                                                   long long cell, bool writable, int rank, int t,
+                                                   double (&c5)[5]) {
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const double s = warp_sum(m[r]);
+    if (lane == 0) red[warp * 5 + r] = s;
+  }
+  __syncthreads();
+  if (t < 5) {
+    double s = 0.0;
+    for (int w = 0; w < WARPS; ++w) s += red[w * 5 + t];
+    red[WARPS * 5 + t] = s;  // this CTA's partial sums
+  }
+  cluster_barrier<C>();
+#pragma unroll
+  for (int r = 0; r < 5; ++r) c5[r] = 0.0;
+  if (args.project) {
+    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < C; ++q) {
+      const double* p = cta_smem<C>(red + WARPS * 5, q);
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        tot[r] += p[r];
+        if (args.compute_targets) tgt[r] += p[5 + r];
+      }
+    }
+    if (!args.compute_targets && args.Utgt) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
+    }
+    if (args.compute_targets && args.Utgt && writable && rank == 0) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        if (t == r) args.Utgt[cell * 5 + r] = tgt[r];  // constant register index
+    }
+    double rhs[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) rhs[r] = tgt[r] - tot[r];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += args.geom.G[r * 5 + k] * rhs[k];
+      c5[r] = s;
+    }
+  }
+  cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
 }
 
 template <typename T, typename TIO, int N, int C, bool kSplit>
@@ -480,50 +538,8 @@ collide_kernel(const CollideArgs args) {
   // Phi g over the row, with v_y = -L + y dv
   double m[5] = {S0, vx * S0, -L * S0 + dv * S1, vz * S0,
                  0.5 * ((vx * vx + vz * vz + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2)};
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    const double s = warp_sum(m[r]);
-    if (lane == 0) red[warp * 5 + r] = s;
-  }
-  __syncthreads();
-  if (t < 5) {
-    double s = 0.0;
-    for (int w = 0; w < WARPS; ++w) s += red[w * 5 + t];
-    red[WARPS * 5 + t] = s;  // this CTA's partial sums
-  }
-  cluster_barrier<C>();
-  double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (args.project) {
-    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int q = 0; q < C; ++q) {
-      const double* p = cta_smem<C>(red + WARPS * 5, q);
-#pragma unroll
-      for (int r = 0; r < 5; ++r) {
-        tot[r] += p[r];
-        if (args.compute_targets) tgt[r] += p[5 + r];
-      }
-    }
-    if (!args.compute_targets && args.Utgt) {
-#pragma unroll
-      for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
-    }
-    if (args.compute_targets && args.Utgt && writable && rank == 0) {
-#pragma unroll
-      for (int r = 0; r < 5; ++r)
-        if (t == r) args.Utgt[cell * 5 + r] = tgt[r];  // constant register index
-    }
-    double rhs[5];
-#pragma unroll
-    for (int r = 0; r < 5; ++r) rhs[r] = tgt[r] - tot[r];
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) s += args.geom.G[r * 5 + k] * rhs[k];
-      c5[r] = s;
-    }
-  }
-  cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
+  double c5[5];
+  cluster_correction<C, WARPS>(args, m, red, cell, writable, rank, t, c5);
   TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
   bool bad = false;
   // Phi^T c at (vx, vy, vz) as a quadratic in the row index y: P0 + P1 y + P2 y^2
@@ -533,6 +549,279 @@ collide_kernel(const CollideArgs args) {
 #pragma unroll
   for (int y = 0; y < N; ++y) {
     const double val = g[y] + (P0 + (double)y * (P1 + (double)y * P2));
+    bad |= !isfinite(val);
+    if (writable) out[(x * N + y) * N + z] = (TIO)val;
+  }
+  if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
+}
+
+// ------------------------------------------------------------------------------------
+// N = 48 and 64 (float32).  One pencil of 48 or 64 complex values takes 96 or 128
+// registers, so the gain accumulator and the spectrum cannot stay in registers as above:
+// the spectrum pencils go to global scratch (each thread reads back only its own pencil:
+// coalesced along kz, L2-resident), the gain accumulator of the CTA's x-slab lives in
+// shared memory, and one x-plane buffer serves every term (two cluster barriers per
+// term).  The epilogue recomputes g in a second sweep instead of keeping N float64 values
+// per thread.  Otherwise the same decomposition and arithmetic as collide_kernel.
+// ------------------------------------------------------------------------------------
+template <int N, int C>
+struct LargeCfg {
+  static constexpr int NP = N / C;
+  static constexpr int THREADS = NP * N;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int VEC = 2;
+  static constexpr int NCH = NP / VEC;
+  static constexpr int RW = N + 1;
+  static constexpr size_t XB = (size_t)NCH * N * RW * VEC;        // float2
+  static constexpr size_t ACC = (size_t)NP * N * N;               // float, [xl][y][z]
+  static constexpr size_t OFF_ACC = XB * sizeof(float2);
+  static constexpr size_t OFF_RED = OFF_ACC + ACC * sizeof(float);
+  static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  static constexpr size_t SMEM = OFF_FLAG + 16;
+  static_assert(THREADS % 32 == 0 && NP % VEC == 0, "whole warps and chunks");
+  static_assert(OFF_RED % 16 == 0, "aligned reduction area");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static __device__ __forceinline__ int elem(int xl, int ky, int k) {
+    return ((xl / VEC) * N + ky) * RW * VEC + k * VEC + xl % VEC;
+  }
+};
+
+template <typename TIO, int N, int C, bool kSplit>
+__global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kernel(const CollideArgs args) {
+  using Cfg = LargeCfg<N, C>;
+  using T = float;
+  using T2 = float2;
+  constexpr int NP = Cfg::NP, WARPS = Cfg::WARPS, VEC = Cfg::VEC, NCH = Cfg::NCH, RW_ = Cfg::RW;
+  constexpr int n = N * N * N;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T2* XB = reinterpret_cast<T2*>(smem_raw);
+  float* accs = reinterpret_cast<float*>(smem_raw + Cfg::OFF_ACC);
+  double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
+
+  const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  const int G = kSplit ? args.groups : 1;
+  long long lc = blockIdx.x / C;
+  int gi = 0;
+  if constexpr (kSplit) {
+    gi = (int)(lc % G);
+    lc /= G;
+  }
+  long long cell = lc;
+  bool writable = true;
+  if (args.cell_idx) {
+    const long long s = args.cell_idx[cell];
+    writable = (s >= 0 && s < args.pool_cells);
+    if (!writable && threadIdx.x == 0) atomicOr(&g_boltz_status, kStatusBadIndex);
+    cell = writable ? s : 0;
+  }
+  const int t = threadIdx.x;
+  const int kyl = t / N, kzt = t % N;
+  const int xlt = (t / (VEC * N)) * VEC + t % VEC, grp = (t / VEC) % N;
+  const int zt = grp;
+  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  const int ky_own = rank * NP + kyl;
+  const int x_own = rank * NP + xlt;
+  // this thread's spectrum pencil (its (ky, kz), all kx) in global scratch
+  T2* spec = reinterpret_cast<T2*>(args.spec) + ((size_t)lc * G + gi) * n + (size_t)ky_own * N * N + kzt;
+
+  T re[N], im[N];
+  const double L = args.geom.L, dv = args.geom.dv;
+  const int lane = t & 31, warp = t >> 5;
+  // ---- forward transform: y pass (thread (x, z)), z pass, x pass ----------------------
+  {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const TIO fv = fin[(x_own * N + y) * N + zt];
+      re[y] = (T)fv;
+      im[y] = T(0);
+      if (args.compute_targets) {
+        s0 += (double)fv;
+        s1 += (double)y * (double)fv;
+        s2 += (double)(y * y) * (double)fv;
+      }
+    }
+    if (args.compute_targets) {
+      const double vx = -L + x_own * dv, vz = -L + zt * dv;
+      const double sy = -L * s0 + dv * s1;
+      const double syy = L * L * s0 - 2.0 * L * dv * s1 + dv * dv * s2;
+      double m[5] = {s0, vx * s0, sy, vz * s0, 0.5 * ((vx * vx + vz * vz) * s0 + syy)};
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const double v = warp_sum(m[r]);
+        if (lane == 0) red[warp * 5 + r] = v;
+      }
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) XB[Cfg::elem(xlt, k, zt)] = make_float2(re[k], im[k]);
+  }
+  __syncthreads();
+  if (args.compute_targets && t < 5) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w * 5 + t];
+    red[(WARPS + 1) * 5 + t] = v;
+  }
+  {
+    T2* col = XB + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const T2 v = col[z * VEC];
+      re[z] = v.x;
+      im[z] = v.y;
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) col[k * VEC] = make_float2(re[k], im[k]);
+  }
+  cluster_barrier<C>();
+  {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const T2* src = XB + Cfg::elem(c * VEC, ky_own, kzt);
+      const uint32_t a = smem_u32(src);
+#pragma unroll
+      for (int q = 0; q < C; ++q) ld_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+    }
+    fft_regs<N, -1>(re, im);
+    const T scale = T(1) / T(n);
+    const bool nyq = (ky_own == N / 2) || (kzt == N / 2);
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      const bool z0 = nyq || (kx == N / 2);
+      spec[(size_t)kx * N] = z0 ? make_float2(0.f, 0.f) : make_float2(re[kx] * scale, im[kx] * scale);
+    }
+  }
+  for (int i = t; i < (int)Cfg::ACC; i += Cfg::THREADS) accs[i] = 0.f;
+  cluster_barrier<C>();  // peers done gathering from this CTA's buffer
+
+  // ---- angular loop --------------------------------------------------------------------
+  const int j0 = kSplit ? (int)(((long long)gi * M_eff) / G) : 0;
+  const int j1 = kSplit ? (int)(((long long)(gi + 1) * M_eff) / G) : M_eff;
+  const bool has_loss = kSplit ? (gi == G - 1) : true;
+  const int nt = (j1 - j0) + (has_loss ? 1 : 0);
+  for (int i = 0; i < nt; ++i) {
+    const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
+    const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+    {  // kx pass with the coefficients: thread (kyl, kz); outputs scattered by x
+      const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
+#pragma unroll
+      for (int kx = 0; kx < N; ++kx) {
+        const T2 c = spec[(size_t)kx * N];
+        const T2 ab = __ldg(tj + kx * N);
+        re[kx] = ab.x * c.x - ab.y * c.y;
+        im[kx] = ab.x * c.y + ab.y * c.x;
+      }
+      fft_regs<N, +1>(re, im);
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const uint32_t a = smem_u32(XB + Cfg::elem(c * VEC, ky_own, kzt));
+#pragma unroll
+        for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+      }
+    }
+    cluster_barrier<C>();
+    {  // kz pass: thread (xl, ky)
+      T2* col = XB + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+      for (int kz = 0; kz < N; ++kz) {
+        const T2 v = col[kz * VEC];
+        re[kz] = v.x;
+        im[kz] = v.y;
+      }
+      fft_regs<N, +1>(re, im);
+#pragma unroll
+      for (int z = 0; z < N; ++z) col[z * VEC] = make_float2(re[z], im[z]);
+    }
+    __syncthreads();
+    {  // ky pass: thread (xl, z); Q+ += w Re Im into shared memory, or keep L in re[]
+      const T2* col = XB + Cfg::elem(xlt, 0, zt);
+#pragma unroll
+      for (int ky = 0; ky < N; ++ky) {
+        const T2 v = col[ky * (RW_ * VEC)];
+        re[ky] = v.x;
+        im[ky] = v.y;
+      }
+      fft_regs<N, +1>(re, im);
+      if (j < M_eff) {
+        float* a = accs + (size_t)xlt * N * N + zt;
+#pragma unroll
+        for (int y = 0; y < N; ++y) a[y * N] += wj * (re[y] * im[y]);
+      }
+    }
+    if (i < nt - 1) cluster_barrier<C>();  // owners done reading before the next scatter
+  }
+
+  const int x = x_own, z = zt;
+  float* acc_row = accs + (size_t)xlt * N * N + z;  // acc_row[y * N], this thread's (x, z) row
+  if constexpr (kSplit) {
+    // partial gain and loss of this group, then the last-arrival count (as collide_kernel)
+    T* part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
+    T* lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x * N + y) * N + z;
+      part[(size_t)gi * n + idx] = acc_row[y * N];
+      if (has_loss) lossp[idx] = re[y];
+    }
+    __threadfence();
+    cluster_barrier<C>();
+    unsigned* flag = reinterpret_cast<unsigned*>(smem_raw + Cfg::OFF_FLAG);
+    if (rank == 0 && t == 0) {
+      const unsigned prev = atomicAdd(&args.arrivals[lc], 1u);
+      const unsigned last = (prev == (unsigned)(G - 1)) ? 1u : 0u;
+      if (last) args.arrivals[lc] = 0u;
+#pragma unroll
+      for (int q = 0; q < C; ++q) *cta_smem<C>(flag, q) = last;
+    }
+    cluster_barrier<C>();
+    if (*flag == 0u) return;
+    __threadfence();
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x * N + y) * N + z;
+      T sum = __ldcg(part + idx);
+      for (int g2 = 1; g2 < G; ++g2) sum += __ldcg(part + (size_t)g2 * n + idx);
+      acc_row[y * N] = sum;
+      re[y] = __ldcg(lossp + idx);
+    }
+  }
+
+  // ---- epilogue (float64), two sweeps over this thread's row --------------------------
+  const double vx = -L + x * dv, vz = -L + z * dv;
+  const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
+  auto gval = [&](int y) {
+    const int idx = (x * N + y) * N + z;
+    const TIO fv = fin[idx];
+    const T q = acc_row[y * N] - (T)fv * re[y];  // Q = Q+ - f L (one rounding in T)
+    double gv = args.s * (double)q;
+    if (args.b != 0.0) gv += args.b * (double)fv;
+    if (fb) gv += args.a * (double)fb[idx];
+    return gv;
+  };
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double gv = gval(y);
+    S0 += gv;
+    S1 += (double)y * gv;
+    S2 += (double)(y * y) * gv;
+  }
+  double m[5] = {S0, vx * S0, -L * S0 + dv * S1, vz * S0,
+                 0.5 * ((vx * vx + vz * vz + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2)};
+  double c5[5];
+  cluster_correction<C, WARPS>(args, m, red, cell, writable, rank, t, c5);
+  TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
+  bool bad = false;
+  const double P0 = c5[0] + c5[1] * vx + c5[3] * vz + 0.5 * c5[4] * (vx * vx + vz * vz + L * L) - c5[2] * L;
+  const double P1 = (c5[2] - c5[4] * L) * dv;
+  const double P2 = 0.5 * c5[4] * dv * dv;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double val = gval(y) + (P0 + (double)y * (P1 + (double)y * P2));
     bad |= !isfinite(val);
     if (writable) out[(x * N + y) * N + z] = (TIO)val;
   }
@@ -614,8 +903,9 @@ boltz_status upload_tables(boltz_grid_s* g) {
   const size_t entries = (size_t)(g->M_eff + 1) * n;
   std::vector<double2> h64;
   std::vector<float2> h32;
+  const bool want64 = collide_supported(g->N, BOLTZ_FP64);  // no float64 path at N = 48, 64
   try {
-    h64.resize(entries);
+    if (want64) h64.resize(entries);
     h32.resize(entries);
   } catch (...) {
     set_error("host staging of the device tables failed");
@@ -631,10 +921,10 @@ boltz_status upload_tables(boltz_grid_s* g) {
           const size_t dst = (size_t)i * n + ((size_t)ky * N + kx) * N + kz;
           const double a = (i < g->M_eff) ? g->alpha[(size_t)i * n + src] : g->D[src];
           const double b = (i < g->M_eff) ? g->alphap[(size_t)i * n + src] : 0.0;
-          h64[dst] = make_double2(a, b);
+          if (want64) h64[dst] = make_double2(a, b);
           h32[dst] = make_float2((float)a, (float)b);
         }
-  if ((e = cudaMalloc(&g->tab64, entries * sizeof(double2))) != cudaSuccess) {
+  if (want64 && (e = cudaMalloc(&g->tab64, entries * sizeof(double2))) != cudaSuccess) {
     set_error(std::string("device tables: ") + cudaGetErrorString(e));
     return BOLTZ_ENOMEM;
   }
@@ -646,7 +936,8 @@ boltz_status upload_tables(boltz_grid_s* g) {
     set_error(std::string("device tables: ") + cudaGetErrorString(e));
     return BOLTZ_ENOMEM;
   }
-  if ((e = cudaMemcpy(g->tab64, h64.data(), entries * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if (want64 && (e = cudaMemcpy(g->tab64, h64.data(), entries * sizeof(double2), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
     return cuda_fail(e, "table upload");
   if ((e = cudaMemcpy(g->tab32, h32.data(), entries * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "table upload");
@@ -714,8 +1005,60 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
   return BOLTZ_OK;
 }
 
+template <typename TIO, int N, int C>
+static boltz_status launch_large_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  using Cfg = LargeCfg<N, C>;
+  const bool split = a.groups > 1;
+  auto kern = split ? collide_large_kernel<TIO, N, C, true> : collide_large_kernel<TIO, N, C, false>;
+  static std::atomic<unsigned long long> prepared[2], unschedulable[2];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const unsigned long long bit = 1ull << (dev & 63);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(C, 1, 1);
+    q.blockDim = dim3(Cfg::THREADS, 1, 1);
+    q.dynamicSmemBytes = Cfg::SMEM;
+    q.attrs = attr;
+    q.numAttrs = 1;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &q);
+    if (e != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      if (dev < 64) unschedulable[split].fetch_or(bit, std::memory_order_release);
+    }
+    if (dev < 64) prepared[split].fetch_or(bit, std::memory_order_release);
+  }
+  if (dev < 64 && (unschedulable[split].load(std::memory_order_acquire) & bit)) {
+    set_error("a thread-block cluster of this size cannot be scheduled on this device");
+    return BOLTZ_EUNSUPPORTED;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
+  cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return cuda_fail(e, "collide launch");
+  return BOLTZ_OK;
+}
+
 bool collide_supported(int N, int prec) {
-  return (N == 8 || N == 16 || N == 24 || N == 32) && (prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT);
+  if (N == 8 || N == 16 || N == 24 || N == 32) return prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT;
+  if (N == 48 || N == 64) return prec == BOLTZ_FP32_FFT;  // float64 pencils of 48/64 do not fit
+  return false;
 }
 
 // Cluster sizes.  float64: the smallest C whose per-CTA slab fits shared memory and
@@ -730,6 +1073,8 @@ int default_cluster(int N, int prec) {
     case 16: return dbl ? 2 : 1;
     case 24: return 3;
     case 32: return 8;
+    case 48: return dbl ? 0 : 8;
+    case 64: return dbl ? 0 : 16;
     default: return 0;
   }
 }
@@ -774,6 +1119,8 @@ static boltz_status dispatch_n(const boltz_grid_s* g, const CollideArgs& a, int6
     if (g->N == 32 && C == 4) return launch_impl<T, TIO, 32, 4>(a, n_cells, st);
     if (g->N == 32 && C == 8) return launch_impl<T, TIO, 32, 8>(a, n_cells, st);
     if (g->N == 32 && C == 16) return launch_impl<T, TIO, 32, 16>(a, n_cells, st);
+    if (g->N == 48 && C == 8) return launch_large_impl<TIO, 48, 8>(a, n_cells, st);
+    if (g->N == 64 && C == 16) return launch_large_impl<TIO, 64, 16>(a, n_cells, st);
   }
   set_error("no collision kernel for this (N, precision, cluster size)");
   return BOLTZ_EUNSUPPORTED;
@@ -827,6 +1174,23 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
     boltz_status r = ensure_split_scratch(g, n_cells, G, prec, stream);
     if (r != BOLTZ_OK) return r;
   }
+  if (g->N > 32) {
+    // spectrum pencils of the large-N kernel: [cells][G][n] float2
+    const size_t need = (size_t)n_cells * G * n * sizeof(float2);
+    if (need > g->spec_cap) {
+      cudaError_t e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return cuda_fail(e, "spectrum scratch sync");
+      cudaFree(g->spec_buf);
+      g->spec_buf = nullptr;
+      g->spec_cap = 0;
+      if (cudaMalloc(&g->spec_buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("spectrum scratch allocation failed");
+        return BOLTZ_ENOMEM;
+      }
+      g->spec_cap = need;
+    }
+  }
   CollideArgs args;
   args.f_in = f_in;
   args.f_base = f_base;
@@ -849,6 +1213,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.arrivals = (G > 1) ? reinterpret_cast<unsigned*>(sb) : nullptr;
   args.part = (G > 1) ? sb + cnt_bytes : nullptr;
   args.loss = (G > 1) ? sb + cnt_bytes + (size_t)n_cells * G * n * tsz : nullptr;
+  args.spec = g->spec_buf;
   if (prec == BOLTZ_FP64) {
     args.tab = g->tab64;
     return f_is_fp64 ? dispatch_n<double, double>(g, args, n_cells, stream, cluster)

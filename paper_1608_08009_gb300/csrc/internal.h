@@ -49,6 +49,9 @@ struct boltz_grid_s {
   // partial gains and loss of split launches (term_groups > 1), grown on demand
   mutable void* split_buf = nullptr;
   mutable size_t split_cap = 0;  // bytes
+  // spectrum pencils of the N = 48, 64 kernel, grown on demand
+  mutable void* spec_buf = nullptr;
+  mutable size_t spec_cap = 0;  // bytes
   // resources of boltz_relax_host (host_io.cpp), created on first use
   static constexpr int kHostBufs = 3;
   void* hbuf[kHostBufs] = {nullptr, nullptr, nullptr};  // device staging, one chunk each

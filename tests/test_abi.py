@@ -56,7 +56,7 @@ def test_argument_errors_without_device(libboltz):
     assert L.boltz_moments(None, None, None, None) == B.BOLTZ_EINVAL
     h = ctypes.c_void_p()
     assert L.boltz_create_grid(15, 8.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
-    assert L.boltz_create_grid(64, 8.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EUNSUPPORTED
+    assert L.boltz_create_grid(96, 8.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EUNSUPPORTED
     assert L.boltz_create_grid(32, -1.0, 1.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
     assert L.boltz_create_grid(32, 8.0, 2.0, 64, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
     assert L.boltz_create_grid(32, 8.0, 1.0, 0, None, ctypes.byref(h)) == B.BOLTZ_EINVAL

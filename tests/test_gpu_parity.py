@@ -378,3 +378,26 @@ def test_term_groups_independent_of_batch_size_and_indexed():
             B.boltz_stream_status()
         assert ei.value.status == 1  # BOLTZ_EINVAL
         assert torch.equal(Qb[2], Qall[2])
+
+
+@pytest.mark.parametrize("N,L,M,groups", [(48, 8.0, 8, 1), (64, 8.0, 8, 1), (48, 8.0, 8, 3), (64, 8.0, 4, 4)])
+def test_large_grids_parity(N, L, M, groups):
+    """48^3 and 64^3 (float32 only: spectrum pencils in global scratch, gain accumulator in
+    shared memory): collide within the float32 bound, one Euler step of relax, and the
+    split launch; float64 is reported unsupported."""
+    cells = 2
+    f = W.two_maxwellians(cells, N, L, seed=101)
+    og = oracle_grid(N, L, M, kind=2)
+    Qref = O.collide(f, og)
+    with B.Grid(N, L, 1.0, M, dirs_kind=2, term_groups=groups) as g:
+        Q = run_collide(g, f, B.BOLTZ_FP32_FFT, fp64=False)
+        assert rel_l2(Q, Qref) <= fp32_tol(f, og)
+        ft = torch.from_numpy(f).cuda()
+        B.boltz_relax(g.batch(cells, B.BOLTZ_FP32_FFT, True), ft, 0.002, 1)
+        B.boltz_stream_status()
+        ref = O.relax(f, og, 0.002, 1)
+        assert rel_l2(ft.cpu().numpy() - f, ref - f) <= fp32_tol(f, og)
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_collide(g.batch(cells, B.BOLTZ_FP64, True), torch.from_numpy(f).cuda(),
+                            torch.empty(cells, N, N, N, dtype=torch.float64, device="cuda"))
+        assert ei.value.status == B.BOLTZ_EUNSUPPORTED
