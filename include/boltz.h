@@ -242,14 +242,20 @@ boltz_status boltz_relax_indexed(const boltz_batch* b, void* f, const int64_t* c
  * the moments the cell has at that step).  The server keeps admitted jobs resident in
  * per-grid device pools of float32 slots, admits queued jobs in arrival order while a
  * slot and the HBM budget (bytes of resident f over all grids) allow, advances all
- * resident jobs of a grid by one indexed launch per boltz_server_step, and copies each
- * finished job back to its host buffer asynchronously.  A job's result does not depend
- * on which other jobs are resident.  All work runs on `stream`; calls are not thread-safe.
+ * resident jobs of a grid by one indexed launch per iteration, and copies each finished
+ * job back to its host buffer asynchronously.  A job's result does not depend on which
+ * other jobs are resident.  Every grid has its own stream (ordered after the work queued
+ * on `stream` at creation) and at most two iterations in flight, so grids advance at
+ * their own pace.  Calls are not thread-safe.
  *   create: grids (one per grid shape a job may use, kept alive by the caller), prec,
  *           dt, budget.  Allocates one pool of budget bytes per grid.
  *   submit: f_host, out_host: N^3 floats each (pinned memory recommended), owned by the
  *           caller until poll reports the job done; returns a job id.
- *   step:   admission, one step of every resident job, retirement; reports counts.
+ *   step:   admission, then one iteration (one step of every resident job, retirement of
+ *           the finished ones) for every grid with resident jobs, waiting where a grid
+ *           already has two iterations in flight; reports counts.
+ *   pump:   as step, but never waits: a grid with two iterations in flight is skipped;
+ *           n_launched = iterations issued (nullable).  For serving loops.
  *   poll:   done = 1 once out_host holds the result. */
 typedef struct boltz_server_s* boltz_server;
 boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec, double dt,
@@ -257,6 +263,7 @@ boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec,
 boltz_status boltz_server_submit(boltz_server s, int grid_index, const float* f_host, float* out_host,
                                  int steps, int64_t* job_id);
 boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued);
+boltz_status boltz_server_pump(boltz_server s, int* n_resident, int* n_queued, int* n_launched);
 boltz_status boltz_server_poll(boltz_server s, int64_t job_id, int* done);
 boltz_status boltz_server_destroy(boltz_server s);
 

@@ -36,7 +36,8 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_grid_info", "boltz_grid_tables", "boltz_version", "boltz_relax_noalloc",
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
             "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
-            "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy")
+            "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
+            "boltz_server_pump")
 
 
 class BoltzError(RuntimeError):
@@ -94,6 +95,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_server_create.argtypes = [P(vp), i32, i32, f64, ctypes.c_size_t, vp, P(vp)]
         L.boltz_server_submit.argtypes = [vp, i32, vp, vp, i32, P(i64)]
         L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
+        L.boltz_server_pump.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.boltz_server_poll.argtypes = [vp, i64, P(i32)]
         L.boltz_server_destroy.argtypes = [vp]
         L.boltz_stream_status.argtypes = [vp]
@@ -108,7 +110,7 @@ def lib() -> ctypes.CDLL:
                      "boltz_relax_noalloc", "boltz_collide_indexed", "boltz_relax_indexed",
                      "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
                      "boltz_server_destroy", "boltz_relax_host", "boltz_plan_create", "boltz_plan_run",
-                     "boltz_plan_group_info", "boltz_plan_destroy"):
+                     "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -253,6 +255,12 @@ class Server:
         r, q = ctypes.c_int(), ctypes.c_int()
         _check(lib().boltz_server_step(self.handle, ctypes.byref(r), ctypes.byref(q)))
         return r.value, q.value
+
+    def pump(self):
+        """Non-blocking step: (resident, queued, iterations launched)."""
+        r, q, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().boltz_server_pump(self.handle, ctypes.byref(r), ctypes.byref(q), ctypes.byref(n)))
+        return r.value, q.value, n.value
 
     def poll(self, job_id: int) -> bool:
         d = ctypes.c_int()

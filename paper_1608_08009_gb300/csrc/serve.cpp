@@ -11,6 +11,11 @@
 // finished jobs with an asynchronous copy back to the caller's host buffer.  Every job
 // is computed by the same per-cell arithmetic whatever else is resident, so its result
 // does not depend on the mix.
+//
+// Each grid has its own stream and at most kDepth iterations in flight, so grids advance
+// at their own pace: cheap 16^3 steps do not wait behind 64^3 steps.  boltz_server_pump
+// never blocks (a grid at full depth is skipped); boltz_server_step waits for room so that
+// every resident job advances by exactly one step per call.
 #include <cstring>
 #include <deque>
 #include <new>
@@ -32,6 +37,9 @@ struct Job {
   int state = 0;               // 0 queued, 1 resident, 2 copying out, 3 finished
 };
 
+constexpr int kDepth = 2;              // iterations in flight per grid
+constexpr int kIdxBufs = kDepth + 1;   // pinned index lists: one more than the depth
+
 struct Pool {
   boltz_grid_s* grid = nullptr;
   size_t n = 0;                 // N^3
@@ -39,9 +47,12 @@ struct Pool {
   int64_t capacity = 0;         // slots
   float* f = nullptr;           // [capacity][n]
   int64_t* idx_dev = nullptr;   // [capacity]
-  int64_t* idx_host[2] = {nullptr, nullptr};  // pinned, alternating
-  cudaEvent_t idx_ready[2] = {nullptr, nullptr};
+  int64_t* idx_host[kIdxBufs] = {};  // pinned, in rotation
+  cudaEvent_t idx_ready[kIdxBufs] = {};
   int idx_turn = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t iter_done[kDepth] = {};  // completion of the iterations in flight, in a ring
+  int iter_head = 0, in_flight = 0;
   std::vector<int64_t> free_slots;
   std::vector<int64_t> resident;  // job ids in admission order
 };
@@ -67,14 +78,18 @@ static boltz_status cuda_err(cudaError_t e, const char* what) {
 
 static void free_server(boltz_server_s* s) {
   if (!s) return;
-  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& p : s->pools)
+    if (p.stream) cudaStreamSynchronize(p.stream);
   for (auto& p : s->pools) {
     cudaFree(p.f);
     cudaFree(p.idx_dev);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kIdxBufs; ++b) {
       cudaFreeHost(p.idx_host[b]);
       if (p.idx_ready[b]) cudaEventDestroy(p.idx_ready[b]);
     }
+    for (int b = 0; b < kDepth; ++b)
+      if (p.iter_done[b]) cudaEventDestroy(p.iter_done[b]);
+    if (p.stream) cudaStreamDestroy(p.stream);
   }
   for (auto& j : s->jobs)
     if (j.done) cudaEventDestroy(j.done);
@@ -127,13 +142,36 @@ boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec,
       set_error(std::string("server pool allocation: ") + cudaGetErrorString(e));
       return BOLTZ_ENOMEM;
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kIdxBufs; ++b) {
       if ((e = cudaMallocHost(&p.idx_host[b], (size_t)p.capacity * sizeof(int64_t))) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&p.idx_ready[b], cudaEventDisableTiming)) != cudaSuccess) {
         free_server(s);
         set_error(std::string("server host buffers: ") + cudaGetErrorString(e));
         return BOLTZ_ENOMEM;
       }
+    }
+    if ((e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      free_server(s);
+      return cuda_err(e, "server stream");
+    }
+    for (int b = 0; b < kDepth; ++b) {
+      if ((e = cudaEventCreateWithFlags(&p.iter_done[b], cudaEventDisableTiming)) != cudaSuccess) {
+        free_server(s);
+        return cuda_err(e, "server events");
+      }
+    }
+    // the grid's stream starts after the work already queued on the caller's stream
+    cudaEvent_t start;
+    if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess) {
+      free_server(s);
+      return cuda_err(e, "server events");
+    }
+    e = cudaEventRecord(start, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p.stream, start, 0);
+    cudaEventDestroy(start);
+    if (e != cudaSuccess) {
+      free_server(s);
+      return cuda_err(e, "server stream order");
     }
     p.free_slots.reserve(p.capacity);
     for (int64_t k = p.capacity - 1; k >= 0; --k) p.free_slots.push_back(k);
@@ -167,7 +205,12 @@ boltz_status boltz_server_submit(boltz_server s, int grid_index, const float* f_
   return BOLTZ_OK;
 }
 
-boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued) {
+}  // extern "C"
+
+// Admission, then one iteration for every grid with resident jobs and room in its depth
+// (blocking: wait for room; otherwise skip the grid).  *launched counts the iterations
+// issued.
+static boltz_status advance(boltz_server s, bool blocking, int* n_resident, int* n_queued, int* launched) {
   if (!s) {
     set_error("null server");
     return BOLTZ_EINVAL;
@@ -181,27 +224,42 @@ boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued) {
     j.slot = p.free_slots.back();
     p.free_slots.pop_back();
     s->used += p.slot_bytes;
-    if ((e = cudaMemcpyAsync(p.f + (size_t)j.slot * p.n, j.in, p.slot_bytes, cudaMemcpyHostToDevice, s->stream)) !=
+    if ((e = cudaMemcpyAsync(p.f + (size_t)j.slot * p.n, j.in, p.slot_bytes, cudaMemcpyHostToDevice, p.stream)) !=
         cudaSuccess)
       return cuda_err(e, "admission copy");
     j.state = 1;
     p.resident.push_back(j.id);
     s->queue.pop_front();
   }
-  // one collision step for every resident job, one indexed launch per grid
+  int issued = 0;
   for (auto& p : s->pools) {
+    // iterations that have finished leave the ring
+    while (p.in_flight > 0) {
+      const int oldest = (p.iter_head - p.in_flight + kDepth) % kDepth;
+      e = cudaEventQuery(p.iter_done[oldest]);
+      if (e == cudaErrorNotReady) break;
+      if (e != cudaSuccess) return cuda_err(e, "iteration event");
+      --p.in_flight;
+    }
     if (p.resident.empty()) continue;
+    if (p.in_flight >= kDepth) {
+      if (!blocking) continue;
+      const int oldest = (p.iter_head - p.in_flight + kDepth) % kDepth;
+      if ((e = cudaEventSynchronize(p.iter_done[oldest])) != cudaSuccess) return cuda_err(e, "iteration event");
+      --p.in_flight;
+    }
+    // one collision step for every resident job of this grid: one indexed launch
     const int b = p.idx_turn;
-    p.idx_turn ^= 1;
+    p.idx_turn = (p.idx_turn + 1) % kIdxBufs;
     if ((e = cudaEventSynchronize(p.idx_ready[b])) != cudaSuccess) return cuda_err(e, "index buffer");
     const int64_t m = (int64_t)p.resident.size();
     for (int64_t k = 0; k < m; ++k) p.idx_host[b][k] = s->jobs[p.resident[k]].slot;
     if ((e = cudaMemcpyAsync(p.idx_dev, p.idx_host[b], (size_t)m * sizeof(int64_t), cudaMemcpyHostToDevice,
-                             s->stream)) != cudaSuccess)
+                             p.stream)) != cudaSuccess)
       return cuda_err(e, "index copy");
-    if ((e = cudaEventRecord(p.idx_ready[b], s->stream)) != cudaSuccess) return cuda_err(e, "index event");
+    if ((e = cudaEventRecord(p.idx_ready[b], p.stream)) != cudaSuccess) return cuda_err(e, "index event");
     boltz_status st = boltz::launch_collide(p.grid, m, s->prec, 0, p.f, nullptr, p.f, 0.0, 1.0, s->dt, nullptr, 1, 1,
-                                            s->stream, p.idx_dev, p.capacity);
+                                            p.stream, p.idx_dev, p.capacity);
     if (st != BOLTZ_OK) return st;
     // retire finished jobs: copy out, release the slot (later copies into it are ordered
     // after this copy on the same stream)
@@ -214,14 +272,18 @@ boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued) {
         continue;
       }
       if ((e = cudaMemcpyAsync(j.out, p.f + (size_t)j.slot * p.n, p.slot_bytes, cudaMemcpyDeviceToHost,
-                               s->stream)) != cudaSuccess)
+                               p.stream)) != cudaSuccess)
         return cuda_err(e, "result copy");
-      if ((e = cudaEventRecord(j.done, s->stream)) != cudaSuccess) return cuda_err(e, "job event");
+      if ((e = cudaEventRecord(j.done, p.stream)) != cudaSuccess) return cuda_err(e, "job event");
       j.state = 2;
       p.free_slots.push_back(j.slot);
       s->used -= p.slot_bytes;
     }
     p.resident.swap(keep);
+    if ((e = cudaEventRecord(p.iter_done[p.iter_head], p.stream)) != cudaSuccess) return cuda_err(e, "iteration event");
+    p.iter_head = (p.iter_head + 1) % kDepth;
+    ++p.in_flight;
+    ++issued;
   }
   if (n_resident) {
     int r = 0;
@@ -229,7 +291,18 @@ boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued) {
     *n_resident = r;
   }
   if (n_queued) *n_queued = (int)s->queue.size();
+  if (launched) *launched = issued;
   return BOLTZ_OK;
+}
+
+extern "C" {
+
+boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued) {
+  return advance(s, true, n_resident, n_queued, nullptr);
+}
+
+boltz_status boltz_server_pump(boltz_server s, int* n_resident, int* n_queued, int* n_launched) {
+  return advance(s, false, n_resident, n_queued, n_launched);
 }
 
 boltz_status boltz_server_poll(boltz_server s, int64_t job_id, int* done) {
