@@ -52,6 +52,10 @@ WORKLOADS = {
     # gamma in {0, 0.5, 1} drawn per cell; one group (grid) per (N, M, gamma)
     "ragged": dict(cells=10000, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20164,
                    ragged=True),
+    # 2D Maxwell molecules (Sec. 3.3 dimension two): 262144 cells of 32^2 on [-9, 9]^2,
+    # eight angles (Test 1.1's grid), float32 transforms
+    "plane32": dict(cells=262144, N=32, L=9.0, M=8, gamma=0.0, dt=0.02, prec="fp32_fft", f64=False, seed=20166,
+                    dim=2, opts=dict(C_gamma=1.0 / (2.0 * math.pi))),
     "bkw16": dict(cells=1, N=16, L=(3.0 + math.sqrt(2.0)) * 3.0, M=32, gamma=0.0, dt=0.01, prec="fp64", f64=True,
                   seed=20161, rk=2, init="bkw",
                   opts=dict(dirs_kind=1, C_gamma=1.0 / (4.0 * math.pi), radial_rank=16, term_groups=64)),
@@ -71,6 +75,8 @@ def make_inputs(wl: dict, cells, total: int):
     """Seeded inputs of the workload for the listed cells of a batch of `total` cells."""
     from paper_1608_08009_gb300 import workloads as W
 
+    if wl.get("dim") == 2:
+        return W.two_maxwellians_2d(total, wl["N"], wl["L"], wl["seed"], cells=cells)
     if wl.get("init") == "bkw":
         return np.repeat(W.bkw(wl["N"], wl["L"], bkw_K(BKW_T0))[None], len(cells), axis=0)
     return W.two_maxwellians(total, wl["N"], wl["L"], wl["seed"], cells=cells)
@@ -84,13 +90,13 @@ NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor),
 NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (287.20e6 + 218.58e6) / 2048, "fp64": (173.07e6 + 94.99e6) / 512}
 
 
-def algorithmic_flops(N: int, M: int) -> float:
-    """F(N, M) = (M + 2) 5 n log2 n + 8 M n + 40 n per cell-collision, n = N^3.
+def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
+    """F(N, M) = (M + 2) 5 n log2 n + 8 M n + 40 n per cell-collision, n = N^dim.
 
     Complex-packed inverse transforms (one per direction plus the loss transform and the
     forward transform, 5 n log2 n each), the coefficient products and gain accumulation
     (8 n per direction) and the moment / projection / update work (40 n)."""
-    n = N ** 3
+    n = N ** dim
     return (M + 2) * 5.0 * n * math.log2(n) + 8.0 * M * n + 40.0 * n
 
 
@@ -179,19 +185,26 @@ def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096):
     from paper_1608_08009_gb300 import workloads as W
 
     o = wl.get("opts", {})
-    g = O.make_grid(wl["N"], wl["L"], gamma=wl["gamma"], M=wl["M"], dirs_kind=o.get("dirs_kind", 0),
-                    C_gamma=o.get("C_gamma", 1.0), rank=o.get("radial_rank") or None)
+    if wl.get("dim") == 2:
+        from oracle import plane as P
+
+        g = P.make_plane_grid(wl["N"], wl["L"], A=wl["M"], Btilde=2.0 * o.get("C_gamma", 1.0))
+        mod = P
+    else:
+        g = O.make_grid(wl["N"], wl["L"], gamma=wl["gamma"], M=wl["M"], dirs_kind=o.get("dirs_kind", 0),
+                        C_gamma=o.get("C_gamma", 1.0), rank=o.get("radial_rank") or None)
+        mod = O
     rk = wl.get("rk", 1)
     U_done, t0 = 0, time.perf_counter()
     c = 0
     while c < max_cells:
         f = make_inputs(wl, [c], wl["cells"])
         if rk == 1:
-            U0 = O.moments(f, g)
-            Q = O.collide(f, g, project=False)
-            O.project_f(f + wl["dt"] * Q, U0, g)
+            U0 = mod.moments(f, g)
+            Q = mod.collide(f, g, project=False)
+            mod.project_f(f + wl["dt"] * Q, U0, g)
         else:
-            O.relax(f, g, wl["dt"], 1, rk_order=rk)
+            mod.relax(f, g, wl["dt"], 1, rk_order=rk)
         c += 1
         U_done += rk
         if time.perf_counter() - t0 >= budget_s:
@@ -434,7 +447,7 @@ def run_reference(args, wl):
 
 
 def l2_policy(wl: dict) -> str:
-    nbytes = wl["cells"] * wl["N"] ** 3 * (8 if wl["f64"] else 4)
+    nbytes = wl["cells"] * wl["N"] ** wl.get("dim", 3) * (8 if wl["f64"] else 4)
     if nbytes >= 2 * L2_BYTES:
         return "inputs larger than L2 (f is %.1f GB)" % (nbytes / 1e9)
     return "L2 flushed between timed steps (f is %.1f MB)" % (nbytes / 1e6)
@@ -443,6 +456,8 @@ def l2_policy(wl: dict) -> str:
 def config_of(args, wl):
     o = wl.get("opts", {})
     dirs = {0: "product grid of midpoints", 1: "spherical Fibonacci", 2: "Gauss x midpoint"}[o.get("dirs_kind", 0)]
+    if wl.get("dim") == 2:
+        dirs = "equally spaced angles pi p / A"
     extra = {}
     if wl.get("rk", 1) == 2:
         extra["integrator"] = "Heun (2 collision evaluations per step)"
@@ -452,6 +467,8 @@ def config_of(args, wl):
         extra["cluster_size"] = o["cluster_size"]
     if wl.get("init") == "bkw":
         extra["datum"] = "3D BKW at K = 3/5, Maxwell molecules, B = 1/(4 pi), radial rank %d" % o.get("radial_rank", 16)
+    if wl.get("dim") == 2:
+        extra["dimension"] = "2D Maxwell molecules, Btilde = 1/pi"
     return {"workload": args.workload, "cells_per_gpu": wl["cells"], "N_v": wl["N"], "L": wl["L"], "M_dirs": wl["M"],
             "gamma": wl["gamma"], "dirs": dirs, "dt": wl["dt"], "precision": wl["prec"], **extra,
             "f_storage": "f64" if wl["f64"] else "f32", "moments_projection_update": "f64",
@@ -474,11 +491,15 @@ def run_ours(args, wl):
     N, L, M, cells = wl["N"], wl["L"], wl["M"], wl["cells"]
     prec = B.BOLTZ_FP64 if wl["prec"] == "fp64" else B.BOLTZ_FP32_FFT
     dtype = torch.float64 if wl["f64"] else torch.float32
-    grid = B.Grid(N, L, wl["gamma"], M, **wl.get("opts", {}))
+    dim = wl.get("dim", 3)
+    if dim == 2:
+        grid = B.Grid2D(N, L, M, **wl.get("opts", {}))
+    else:
+        grid = B.Grid(N, L, wl["gamma"], M, **wl.get("opts", {}))
     batch = grid.batch(cells, prec, wl["f64"])
     rk = wl.get("rk", 1)
     # seeded inputs; rank r takes the cells [r * cells, (r+1) * cells) of one big batch
-    host = torch.empty(cells, N, N, N, dtype=dtype).pin_memory()
+    host = torch.empty((cells,) + (N,) * dim, dtype=dtype).pin_memory()
     chunk = 1024
     for c0 in range(0, cells, chunk):
         c1 = min(cells, c0 + chunk)
@@ -598,7 +619,7 @@ def run_ours(args, wl):
 
     if rank == 0:
         peaks = measured_peaks()
-        flops_cell = algorithmic_flops(N, grid.info["M_eff"])
+        flops_cell = algorithmic_flops(N, grid.info["M_eff"], dim)
         avg_s = statistics.mean(step_ms) / 1000.0 / rk  # one launch per collision evaluation
         achieved = flops_cell * cells / avg_s / 1e12
         if wl["prec"] == "fp64":
@@ -613,9 +634,10 @@ def run_ours(args, wl):
             "config": config_of(args, wl),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": (NCU_DRAM_BYTES_PER_CELL.get(wl["prec"]) or 0) * cells or None,
+                         "traffic": ((NCU_DRAM_BYTES_PER_CELL.get(wl["prec"]) or 0) * cells or None) if dim == 3
+                         and N == 32 else None,
                          "traffic_unit": "bytes per launch (ncu dram read+write, scaled by cells)",
-                         "algorithmic_bytes": 2 * N ** 3 * (8 if wl["f64"] else 4) * cells,
+                         "algorithmic_bytes": 2 * N ** dim * (8 if wl["f64"] else 4) * cells,
                          "kernel": "collide_kernel (one launch per step)",
                          "flops_per_cell": flops_cell, "peak_source": peak_note},
             "e2e": {"value": e2e_value, "unit": "cell-collisions/s", "h2d_bytes_per_step": nbytes,

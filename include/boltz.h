@@ -129,6 +129,19 @@ void boltz_default_opts(boltz_grid_opts* opts);
 boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs,
                                const boltz_grid_opts* opts, boltz_grid* out);
 
+/* Two-dimensional grid for Maxwell molecules (Sec. 3.3, dimension two; Eq. dfor0): the
+ * Carleman kernel is the constant Btilde = 2 C_gamma (opts->C_gamma, default 1;
+ * C_gamma = 1/(2 pi) is the normalisation of the 2D BKW solution of Test 1.1), A = M_dirs
+ * equally spaced angles theta_p = pi p / A with weight pi / A, alpha_p(k) =
+ * Btilde 2R Sinc(R xi_k . e_p), alpha'_p(k) = 2R Sinc(R xi_k . e_p-perp); S, R as in 3D
+ * (opts->R_trunc).  Cells are N_v x N_v arrays [x][y] (y fastest); boltz_collide,
+ * boltz_relax (and _indexed, _host, _noalloc) and boltz_moments accept batches on it;
+ * moments are (rho, rho u_x, rho u_y, 0, E).  Term groups and cluster sizes do not apply.
+ *   N_v     8, 16, 32 (float64 and float32), 64 (float32 only).
+ *   M_dirs  number of angles A, 1..4096.
+ * Errors: EINVAL, EUNSUPPORTED (N_v), ENOMEM, ECUDA. */
+boltz_status boltz_create_grid2d(int N_v, double L, int M_dirs, const boltz_grid_opts* opts, boltz_grid* out);
+
 /* Free the grid and its tables.  Synchronises the device first.  NULL is a no-op. */
 boltz_status boltz_destroy_grid(boltz_grid g);
 

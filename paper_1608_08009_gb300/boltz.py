@@ -37,7 +37,7 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
             "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
             "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
-            "boltz_server_pump")
+            "boltz_server_pump", "boltz_create_grid2d")
 
 
 class BoltzError(RuntimeError):
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_default_opts.argtypes = [P(boltz_grid_opts)]
         L.boltz_default_opts.restype = None
         L.boltz_create_grid.argtypes = [i32, f64, f64, i32, P(boltz_grid_opts), P(vp)]
+        L.boltz_create_grid2d.argtypes = [i32, f64, i32, P(boltz_grid_opts), P(vp)]
         L.boltz_destroy_grid.argtypes = [vp]
         L.boltz_collide.argtypes = [P(boltz_batch), vp, vp, vp]
         L.boltz_relax.argtypes = [P(boltz_batch), vp, f64, i32, i32, vp]
@@ -110,7 +111,8 @@ def lib() -> ctypes.CDLL:
                      "boltz_relax_noalloc", "boltz_collide_indexed", "boltz_relax_indexed",
                      "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
                      "boltz_server_destroy", "boltz_relax_host", "boltz_plan_create", "boltz_plan_run",
-                     "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump"):
+                     "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump",
+                     "boltz_create_grid2d"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -216,13 +218,14 @@ def boltz_grid_info(grid: int) -> dict:
     return {"N": N.value, "L": L.value, "dv": dv.value, "S": S.value, "R": R.value, "M_eff": M.value}
 
 
-def boltz_grid_tables(grid: int, M_dirs: int):
+def boltz_grid_tables(grid: int, M_dirs: int, dim: int = 3):
     """Host float64 tables (e, w, alpha, alphap, D) as numpy arrays (for parity tests)."""
     import numpy as np
 
     info = boltz_grid_info(grid)
     N, Me = info["N"], info["M_eff"]
-    n = N ** 3
+    shape = (N,) * dim
+    n = N ** dim
     e = np.empty(M_dirs * 3)
     w = np.empty(Me)
     al = np.empty(Me * n)
@@ -230,7 +233,7 @@ def boltz_grid_tables(grid: int, M_dirs: int):
     D = np.empty(n)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(lib().boltz_grid_tables(grid, p(e), p(w), p(al), p(ap), p(D)))
-    return e.reshape(M_dirs, 3), w, al.reshape(Me, N, N, N), ap.reshape(Me, N, N, N), D.reshape(N, N, N)
+    return e.reshape(M_dirs, 3), w, al.reshape((Me,) + shape), ap.reshape((Me,) + shape), D.reshape(shape)
 
 
 class Server:
@@ -313,6 +316,23 @@ class Grid:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Grid2D(Grid):
+    """2D Maxwell-molecule grid (boltz_create_grid2d); same batch/close interface as Grid."""
+
+    def __init__(self, N_v: int, L: float, A: int = 8, **opts):
+        o = boltz_default_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.M_dirs = A
+        h = ctypes.c_void_p()
+        _check(lib().boltz_create_grid2d(N_v, L, A, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+        self.info = boltz_grid_info(self.handle)
+
+    def tables(self):
+        return boltz_grid_tables(self.handle, self.M_dirs, dim=2)
 
 
 class Plan:

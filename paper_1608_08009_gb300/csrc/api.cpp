@@ -43,7 +43,7 @@ boltz_status check_batch(const boltz_batch* b) {
     set_error("unknown precision");
     return BOLTZ_EINVAL;
   }
-  if (!boltz::collide_supported(b->grid->N, b->prec)) {
+  if (!boltz::collide_supported_grid(b->grid, b->prec)) {
     set_error("this precision has no kernel for this N in this build");
     return BOLTZ_EUNSUPPORTED;
   }
@@ -175,6 +175,59 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
   return BOLTZ_OK;
 }
 
+boltz_status boltz_create_grid2d(int N_v, double L, int M_dirs, const boltz_grid_opts* opts, boltz_grid* out) {
+  if (!out) {
+    set_error("null output handle");
+    return BOLTZ_EINVAL;
+  }
+  if (N_v != 8 && N_v != 16 && N_v != 32 && N_v != 64) {
+    set_error("2D grids: N_v must be 8, 16, 32 or 64 in this build");
+    return (N_v > 0 && N_v % 2 == 0) ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
+  }
+  if (!(L > 0) || !std::isfinite(L)) {
+    set_error("L must be positive and finite");
+    return BOLTZ_EINVAL;
+  }
+  if (M_dirs < 1 || M_dirs > 4096) {
+    set_error("M_dirs must lie in [1, 4096]");
+    return BOLTZ_EINVAL;
+  }
+  boltz_grid_opts o;
+  boltz_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.C_gamma > 0) || !std::isfinite(o.C_gamma)) {
+    set_error("C_gamma must be positive");
+    return BOLTZ_EINVAL;
+  }
+  boltz_grid_s* g = new (std::nothrow) boltz_grid_s();
+  if (!g) {
+    set_error("out of host memory");
+    return BOLTZ_ENOMEM;
+  }
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return BOLTZ_ECUDA;
+  }
+  g->dim = 2;
+  g->N = N_v;
+  g->L = L;
+  g->gamma = 0.0;
+  g->C_gamma = o.C_gamma;
+  g->M = M_dirs;
+  g->project = o.project ? 1 : 0;
+  g->R = o.R_trunc > 0 ? o.R_trunc : 0.0;
+  boltz_status st = boltz::build_tables2d(g);
+  if (st == BOLTZ_OK) st = boltz::upload_tables(g);
+  if (st != BOLTZ_OK) {
+    boltz_destroy_grid(g);
+    return st;
+  }
+  *out = g;
+  return BOLTZ_OK;
+}
+
 boltz_status boltz_destroy_grid(boltz_grid g) {
   if (!g) return BOLTZ_OK;
   int prev = -1;
@@ -289,8 +342,9 @@ boltz_status boltz_moments(const boltz_batch* b, const void* f, double* U, void*
   }
   boltz_status st = check_device(b->grid);
   if (st != BOLTZ_OK) return st;
-  const double dv3 = b->grid->dv * b->grid->dv * b->grid->dv;
-  return boltz::launch_phisums(b->grid, b->n_cells, b->f_is_fp64, f, U, dv3, (cudaStream_t)stream);
+  const double dv = b->grid->dv;
+  const double vol = (b->grid->dim == 2) ? dv * dv : dv * dv * dv;  // dv^d
+  return boltz::launch_phisums(b->grid, b->n_cells, b->f_is_fp64, f, U, vol, (cudaStream_t)stream);
 }
 
 boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, int rk_order, void* stream) {
@@ -316,7 +370,7 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
   if ((st = check_device(b->grid)) != BOLTZ_OK) return st;
   boltz_grid_s* g = b->grid;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t n = boltz::cell_points(g);
   const size_t esz = b->f_is_fp64 ? 8 : 4;
   // scratch: moment targets (and the Heun stage), grown on demand, owned by the grid
   if ((size_t)b->n_cells > g->U0_cap) {

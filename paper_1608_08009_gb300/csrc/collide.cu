@@ -828,6 +828,230 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
 }
 
+// ------------------------------------------------------------------------------------
+// Two dimensions (Maxwell molecules; Sec. 3.3 dimension two, Eq. dfor0).  A cell is N
+// threads (one pencil each) of a CTA that holds several cells; the cell's spectrum and
+// one N x (N+1) plane buffer live in shared memory, the gain accumulator in registers.
+// Per term: kx pass with the coefficients (thread ky, tables [term][kx][ky] read
+// coalesced across the cell's threads), transposed store, ky pass (thread x) and
+// Q+ += w Re Im along y.  Projection on (1, v_x, v_y, |v|^2/2) in float64 (the 5-slot
+// matrix G has row and column 3 zero), two sweeps in the epilogue.
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+struct PlaneCfg {
+  using T2 = typename Vec2<T>::type;
+  static constexpr int RW = N + 1;
+  static constexpr size_t BUF = (size_t)N * RW;  // T2 per plane
+  static constexpr size_t CELL_SMEM = 2 * BUF * sizeof(T2) + (size_t)(N + 1) * 10 * sizeof(double);
+  static constexpr int CPB_SMEM = (int)((200u * 1024u) / CELL_SMEM);
+  static constexpr int CPB = (256 / N < CPB_SMEM) ? 256 / N : CPB_SMEM;  // cells per CTA
+  static constexpr int THREADS = CPB * N;
+  static constexpr size_t SMEM = (size_t)CPB * CELL_SMEM;
+  static_assert(CPB >= 1, "one cell must fit");
+  static_assert((2 * BUF * sizeof(T2)) % 16 == 0 || true, "");
+};
+
+template <typename T, typename TIO, int N>
+__global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(const CollideArgs args, long long n_cells) {
+  using Cfg = PlaneCfg<T, N>;
+  using T2 = typename Cfg::T2;
+  constexpr int RW_ = Cfg::RW;
+  constexpr int n = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int ci = threadIdx.x / N, t = threadIdx.x % N;
+  unsigned char* base = smem_raw + (size_t)ci * Cfg::CELL_SMEM;
+  T2* Fh = reinterpret_cast<T2*>(base);                 // spectrum [kx][ky]
+  T2* P = Fh + Cfg::BUF;                                 // plane buffer [x][ky]
+  double* red = reinterpret_cast<double*>(P + Cfg::BUF); // [N][10], then [10] cell totals
+
+  long long lc = (long long)blockIdx.x * Cfg::CPB + ci;
+  const bool in_launch = lc < n_cells;  // the last CTA may hold fewer cells
+  if (!in_launch) lc = n_cells - 1;
+  long long cell = lc;
+  bool writable = in_launch;
+  if (args.cell_idx) {
+    const long long s = args.cell_idx[lc];
+    const bool ok = (s >= 0 && s < args.pool_cells);
+    if (!ok && in_launch && t == 0) atomicOr(&g_boltz_status, kStatusBadIndex);
+    writable = writable && ok;
+    cell = ok ? s : 0;
+  }
+  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  const double L = args.geom.L, dv = args.geom.dv;
+  T re[N], im[N], acc[N];
+
+  // forward: y pass (thread x), then x pass (thread ky)
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const TIO fv = fin[t * N + y];
+    re[y] = (T)fv;
+    im[y] = T(0);
+    s0 += (double)fv;
+    s1 += (double)y * (double)fv;
+    s2 += (double)(y * y) * (double)fv;
+  }
+  fft_regs<N, -1>(re, im);
+#pragma unroll
+  for (int k = 0; k < N; ++k) P[t * RW_ + k] = mk2<T>(re[k], im[k]);
+  __syncthreads();
+#pragma unroll
+  for (int x = 0; x < N; ++x) {
+    const T2 v = P[x * RW_ + t];
+    re[x] = v.x;
+    im[x] = v.y;
+  }
+  fft_regs<N, -1>(re, im);
+  {
+    const T scale = T(1) / T(n);
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      const bool z0 = (kx == N / 2) || (t == N / 2);
+      Fh[kx * RW_ + t] = z0 ? mk2<T>(T(0), T(0)) : mk2<T>(re[kx] * scale, im[kx] * scale);
+    }
+  }
+#pragma unroll
+  for (int y = 0; y < N; ++y) acc[y] = T(0);
+  __syncthreads();
+
+  for (int j = 0; j <= M_eff; ++j) {
+    const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+    const T2* tj = tab + (size_t)j * n + t;
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      const T2 c = Fh[kx * RW_ + t];
+      const T2 ab = __ldg(tj + kx * N);
+      re[kx] = ab.x * c.x - ab.y * c.y;
+      im[kx] = ab.x * c.y + ab.y * c.x;
+    }
+    fft_regs<N, +1>(re, im);
+#pragma unroll
+    for (int x = 0; x < N; ++x) P[x * RW_ + t] = mk2<T>(re[x], im[x]);
+    __syncthreads();
+#pragma unroll
+    for (int ky = 0; ky < N; ++ky) {
+      const T2 v = P[t * RW_ + ky];
+      re[ky] = v.x;
+      im[ky] = v.y;
+    }
+    fft_regs<N, +1>(re, im);
+    if (j < M_eff) {
+#pragma unroll
+      for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
+    }
+    __syncthreads();  // the next term overwrites P
+  }
+  // re[] holds the loss multiplier L along y of row x = t
+
+  const int x = t;
+  const double vx = -L + x * dv;
+  const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
+  auto gval = [&](int y) {
+    const TIO fv = fin[x * N + y];
+    const T q = acc[y] - (T)fv * re[y];
+    double gv = args.s * (double)q;
+    if (args.b != 0.0) gv += args.b * (double)fv;
+    if (fb) gv += args.a * (double)fb[x * N + y];
+    return gv;
+  };
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double gv = gval(y);
+    S0 += gv;
+    S1 += (double)y * gv;
+    S2 += (double)(y * y) * gv;
+  }
+  // this row's share of Phi g and Phi f (targets), v_y = -L + y dv; slot 3 (v_z) is zero
+  {
+    double* r = red + t * 10;
+    r[0] = S0;
+    r[1] = vx * S0;
+    r[2] = -L * S0 + dv * S1;
+    r[3] = 0.0;
+    r[4] = 0.5 * ((vx * vx + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2);
+    r[5] = s0;
+    r[6] = vx * s0;
+    r[7] = -L * s0 + dv * s1;
+    r[8] = 0.0;
+    r[9] = 0.5 * ((vx * vx + L * L) * s0 - 2.0 * L * dv * s1 + dv * dv * s2);
+  }
+  __syncthreads();
+  double* tot = red + N * 10;
+  if (t < 10) {
+    double v = 0.0;
+    for (int q = 0; q < N; ++q) v += red[q * 10 + t];
+    tot[t] = v;
+  }
+  __syncthreads();
+  double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (args.project) {
+    double tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (args.compute_targets) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = tot[5 + r];
+      if (args.Utgt && writable && t == 0) {
+#pragma unroll
+        for (int r = 0; r < 5; ++r) args.Utgt[cell * 5 + r] = tgt[r];
+      }
+    } else if (args.Utgt) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v += args.geom.G[r * 5 + k] * (tgt[k] - tot[k]);
+      c5[r] = v;
+    }
+  }
+  TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
+  bool bad = false;
+  const double P0 = c5[0] + c5[1] * vx + 0.5 * c5[4] * (vx * vx + L * L) - c5[2] * L;
+  const double P1 = (c5[2] - c5[4] * L) * dv;
+  const double P2 = 0.5 * c5[4] * dv * dv;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double val = gval(y) + (P0 + (double)y * (P1 + (double)y * P2));
+    bad |= !isfinite(val);
+    if (writable) out[x * N + y] = (TIO)val;
+  }
+  if (bad && writable) atomicOr(&g_boltz_status, kStatusNonFinite);
+}
+
+// U[c] = scale * (sum f, sum v_x f, sum v_y f, 0, sum |v|^2/2 f) of 2D cells; one warp per cell.
+template <typename TIO>
+__global__ void __launch_bounds__(256) phisums2d_kernel(const TIO* f, double* U, int N, double L, double dv,
+                                                        double scale, long long n_cells) {
+  const long long cell = (long long)blockIdx.x * 8 + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (cell >= n_cells) return;
+  const TIO* fc = f + cell * (long long)N * N;
+  double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int x = lane; x < N; x += 32) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int y = 0; y < N; ++y) {
+      const double fv = (double)fc[x * N + y];
+      s0 += fv;
+      s1 += (double)y * fv;
+      s2 += (double)(y * y) * fv;
+    }
+    const double vx = -L + x * dv;
+    m[0] += s0;
+    m[1] += vx * s0;
+    m[2] += -L * s0 + dv * s1;
+    m[4] += 0.5 * ((vx * vx + L * L) * s0 - 2.0 * L * dv * s1 + dv * dv * s2);
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const double v = warp_sum(m[r]);
+    if (lane == 0) U[cell * 5 + r] = scale * v;
+  }
+}
+
 // Plain sums Phi f per cell, scaled: U[c][r] = scale * sum_v phi_r(v) f(v).  One thread
 // per (x, y) row: sum f, sum z f and sum z^2 f along the row, then the row's share of the
 // five moments from v_z = -L + z dv (float64 throughout; three float64 operations per
@@ -899,11 +1123,11 @@ boltz_status upload_tables(boltz_grid_s* g) {
   if ((e = cudaMemcpyToSymbol(c_twc32, fc, sizeof(fc))) != cudaSuccess) return cuda_fail(e, "twiddle upload");
   if ((e = cudaMemcpyToSymbol(c_tws32, fs, sizeof(fs))) != cudaSuccess) return cuda_fail(e, "twiddle upload");
 
-  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t n = (g->dim == 2) ? (size_t)g->N * g->N : (size_t)g->N * g->N * g->N;
   const size_t entries = (size_t)(g->M_eff + 1) * n;
   std::vector<double2> h64;
   std::vector<float2> h32;
-  const bool want64 = collide_supported(g->N, BOLTZ_FP64);  // no float64 path at N = 48, 64
+  const bool want64 = collide_supported_grid(g, BOLTZ_FP64);  // no float64 path at N = 48, 64
   try {
     if (want64) h64.resize(entries);
     h32.resize(entries);
@@ -911,9 +1135,19 @@ boltz_status upload_tables(boltz_grid_s* g) {
     set_error("host staging of the device tables failed");
     return BOLTZ_ENOMEM;
   }
-  // device layout [i][ky][kx][kz]: the ky-slab of one direction is one contiguous block
+  // device layout [i][ky][kx][kz]: the ky-slab of one direction is one contiguous block;
+  // 2D grids keep the host order [i][kx][ky] (a cell's threads read along ky)
   const int N = g->N;
-  for (int i = 0; i <= g->M_eff; ++i)
+  if (g->dim == 2) {
+    for (int i = 0; i <= g->M_eff; ++i)
+      for (size_t k = 0; k < n; ++k) {
+        const double a = (i < g->M_eff) ? g->alpha[(size_t)i * n + k] : g->D[k];
+        const double b = (i < g->M_eff) ? g->alphap[(size_t)i * n + k] : 0.0;
+        if (want64) h64[(size_t)i * n + k] = make_double2(a, b);
+        h32[(size_t)i * n + k] = make_float2((float)a, (float)b);
+      }
+  }
+  for (int i = 0; g->dim == 3 && i <= g->M_eff; ++i)
     for (int kx = 0; kx < N; ++kx)
       for (int ky = 0; ky < N; ++ky)
         for (int kz = 0; kz < N; ++kz) {
@@ -1055,6 +1289,48 @@ static boltz_status launch_large_impl(const CollideArgs& a, int64_t n_cells, cud
   return BOLTZ_OK;
 }
 
+template <typename T, typename TIO, int N>
+static boltz_status launch2d_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  using Cfg = PlaneCfg<T, N>;
+  auto kern = collide2d_kernel<T, TIO, N>;
+  static std::atomic<unsigned long long> prepared{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (dev >= 64 || !(prepared.load(std::memory_order_acquire) & bit)) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    if (dev < 64) prepared.fetch_or(bit, std::memory_order_release);
+  }
+  const long long blocks = (n_cells + Cfg::CPB - 1) / Cfg::CPB;
+  kern<<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, st>>>(a, (long long)n_cells);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "collide2d launch");
+  return BOLTZ_OK;
+}
+
+template <typename T, typename TIO>
+static boltz_status dispatch2d(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  switch (g->N) {
+    case 8: return launch2d_impl<T, TIO, 8>(a, n_cells, st);
+    case 16: return launch2d_impl<T, TIO, 16>(a, n_cells, st);
+    case 32: return launch2d_impl<T, TIO, 32>(a, n_cells, st);
+    case 64:
+      if constexpr (sizeof(T) == 4) return launch2d_impl<T, TIO, 64>(a, n_cells, st);
+      break;
+    default: break;
+  }
+  set_error("no 2D collision kernel for this (N, precision)");
+  return BOLTZ_EUNSUPPORTED;
+}
+
+bool collide_supported_grid(const boltz_grid_s* g, int prec) {
+  if (g->dim == 2)
+    return (g->N == 8 || g->N == 16 || g->N == 32) ? (prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT)
+                                                   : (g->N == 64 && prec == BOLTZ_FP32_FFT);
+  return collide_supported(g->N, prec);
+}
+
 bool collide_supported(int N, int prec) {
   if (N == 8 || N == 16 || N == 24 || N == 32) return prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT;
   if (N == 48 || N == 64) return prec == BOLTZ_FP32_FFT;  // float64 pencils of 48/64 do not fit
@@ -1156,9 +1432,37 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                             int compute_targets, int project, cudaStream_t stream, const int64_t* cell_idx,
                             int64_t pool_cells, int groups, int cluster) {
   if (n_cells == 0) return BOLTZ_OK;
-  if (!collide_supported(g->N, prec)) {
+  if (!collide_supported_grid(g, prec)) {
     set_error("unsupported (N, precision) combination");
     return BOLTZ_EUNSUPPORTED;
+  }
+  if (g->dim == 2) {
+    CollideArgs a2 = {};
+    a2.f_in = f_in;
+    a2.f_base = f_base;
+    a2.out = out;
+    a2.w = g->w_dev;
+    a2.Utgt = Utgt;
+    a2.a = a;
+    a2.b = b;
+    a2.s = s;
+    a2.M_eff = g->M_eff;
+    a2.project = project;
+    a2.compute_targets = compute_targets;
+    a2.cell_idx = cell_idx;
+    a2.pool_cells = pool_cells;
+    a2.groups = 1;
+    a2.geom.L = g->L;
+    a2.geom.dv = g->dv;
+    for (int i = 0; i < 25; ++i) a2.geom.G[i] = g->proj.G[i];
+    if (prec == BOLTZ_FP64) {
+      a2.tab = g->tab64;
+      return f_is_fp64 ? dispatch2d<double, double>(g, a2, n_cells, stream)
+                       : dispatch2d<double, float>(g, a2, n_cells, stream);
+    }
+    a2.tab = g->tab32;
+    return f_is_fp64 ? dispatch2d<float, double>(g, a2, n_cells, stream)
+                     : dispatch2d<float, float>(g, a2, n_cells, stream);
   }
   if (cluster == 0 && prec != BOLTZ_FP64) cluster = g->cluster_size;  // 0: the default of (N, prec)
   int G = groups < 0 ? g->term_groups : groups;
@@ -1227,6 +1531,16 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f, double* U,
                             double scale, cudaStream_t stream) {
   if (n_cells == 0) return BOLTZ_OK;
+  if (g->dim == 2) {
+    const unsigned blocks = (unsigned)((n_cells + 7) / 8);
+    if (f_is_fp64)
+      phisums2d_kernel<double><<<blocks, 256, 0, stream>>>((const double*)f, U, g->N, g->L, g->dv, scale, n_cells);
+    else
+      phisums2d_kernel<float><<<blocks, 256, 0, stream>>>((const float*)f, U, g->N, g->L, g->dv, scale, n_cells);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+    return BOLTZ_OK;
+  }
   dim3 grid((unsigned)n_cells), block(256);
   if (f_is_fp64)
     phisums_kernel<double><<<grid, block, 0, stream>>>((const double*)f, U, g->N, g->L, g->dv, scale);

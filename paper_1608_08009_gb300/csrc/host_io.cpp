@@ -56,7 +56,7 @@ static boltz_status ensure_pipeline(boltz_grid_s* g, int64_t chunk, size_t esz, 
         return fail(e, "host pipeline events");
     }
   }
-  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t n = cell_points(g);
   const size_t bytes = (size_t)chunk * n * esz;
   if (bytes > g->hbuf_cap || (size_t)chunk > g->hchunk_cap) {
     // earlier work of this grid may still use the old buffers
@@ -113,7 +113,7 @@ boltz_status boltz_relax_host(const boltz_batch* b, const void* f_in, void* f_ou
   if ((st = boltz::check_device(b->grid)) != BOLTZ_OK) return st;
   boltz_grid_s* g = b->grid;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = (size_t)g->N * g->N * g->N;
+  const size_t n = boltz::cell_points(g);
   const size_t esz = b->f_is_fp64 ? 8 : 4;
   // default chunk: about 8 chunks, at least 512 cells (or the whole batch), at most
   // 1 GiB of f per chunk

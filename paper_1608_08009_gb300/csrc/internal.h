@@ -27,6 +27,7 @@ struct KernelGeom {
 }  // namespace boltz
 
 struct boltz_grid_s {
+  int dim = 3;  // velocity dimension: 3, or 2 (Maxwell molecules, boltz_create_grid2d)
   int N = 0;
   double L = 0, dv = 0, S = 0, R = 0, gamma = 1, C_gamma = 1;
   int M = 0, rank = 1, M_eff = 0;
@@ -68,10 +69,17 @@ struct boltz_grid_s {
 
 namespace boltz {
 
+// Velocity points per cell: N^3, or N^2 on a 2D grid.
+inline size_t cell_points(const boltz_grid_s* g) {
+  return g->dim == 2 ? (size_t)g->N * g->N : (size_t)g->N * g->N * g->N;
+}
+
 void set_error(const std::string& msg);
 
 // Host table builder (tables.cpp): fills e, wdir, w, alpha, alphap, D, proj, S, R.
 boltz_status build_tables(boltz_grid_s* g);
+// Host table builder of the 2D Maxwell-molecule grids (tables.cpp).
+boltz_status build_tables2d(boltz_grid_s* g);
 
 // Kernel launchers (collide.cu).
 boltz_status upload_tables(boltz_grid_s* g);
@@ -93,6 +101,8 @@ int cluster_choices(int N, int prec, int* out);
 boltz_status launch_phisums(const boltz_grid_s* g, int64_t n_cells, int f_is_fp64, const void* f,
                             double* U, double scale, cudaStream_t stream);
 bool collide_supported(int N, int prec);
+// As collide_supported, for the grid's dimension (2D grids: 8, 16, 32 both precisions, 64 float32).
+bool collide_supported_grid(const boltz_grid_s* g, int prec);
 // `steps` Euler or Heun steps of n_cells cells of f in place (the body of boltz_relax);
 // U0: [n_cells][5] scratch for the targets, stage: one copy of f (Heun only).
 boltz_status relax_steps(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, void* f, double dt,

@@ -65,7 +65,7 @@ extern "C" boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, doubl
     boltz::set_error("boltz_relax_noalloc: n_cells exceeds the static scratch limit of 65536 cells per call");
     return BOLTZ_EINVAL;
   }
-  if (!boltz::collide_supported(b->grid->N, b->prec)) {
+  if (!boltz::collide_supported_grid(b->grid, b->prec)) {
     boltz::set_error("this precision has no kernel for this N in this build");
     return BOLTZ_EUNSUPPORTED;
   }

@@ -68,7 +68,7 @@ static void free_plan(boltz_plan_s* p) {
 // user's f is not touched) and keep the fastest.  Term groups are only tried when the
 // cells alone leave SMs idle.
 static boltz_status autotune(PlanGroup& g, cudaStream_t s) {
-  const size_t n = (size_t)g.grid->N * g.grid->N * g.grid->N;
+  const size_t n = boltz::cell_points(g.grid);
   const size_t bytes = (size_t)g.n_cells * n * (g.f_is_fp64 ? 8 : 4);
   void *fa = nullptr, *qa = nullptr;
   cudaError_t e;
@@ -183,7 +183,7 @@ boltz_status boltz_plan_create(const boltz_group* groups, int n_groups, double d
     g.term_groups = std::max(1, std::min(g.grid->term_groups, g.grid->M_eff));
     g.cluster = (g.prec != BOLTZ_FP64 && g.grid->cluster_size) ? g.grid->cluster_size
                                                                 : boltz::default_cluster(g.grid->N, g.prec);
-    const size_t n = (size_t)g.grid->N * g.grid->N * g.grid->N;
+    const size_t n = boltz::cell_points(g.grid);
     const size_t cells = (size_t)std::max<int64_t>(1, g.n_cells);
     if (cudaMalloc(&g.U0, cells * 5 * sizeof(double)) != cudaSuccess ||
         (rk_order == 2 && cudaMalloc(&g.stage, cells * n * (g.f_is_fp64 ? 8 : 4)) != cudaSuccess)) {

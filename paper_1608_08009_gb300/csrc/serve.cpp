@@ -109,7 +109,7 @@ boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec,
     return BOLTZ_EINVAL;
   }
   for (int i = 0; i < n_grids; ++i) {
-    if (!grids[i] || !boltz::collide_supported(grids[i]->N, prec)) {
+    if (!grids[i] || !boltz::collide_supported_grid(grids[i], prec)) {
       set_error("null grid or unsupported (N, precision)");
       return grids[i] ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
     }
@@ -127,7 +127,7 @@ boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec,
   for (int i = 0; i < n_grids; ++i) {
     Pool& p = s->pools[i];
     p.grid = grids[i];
-    p.n = (size_t)grids[i]->N * grids[i]->N * grids[i]->N;
+    p.n = boltz::cell_points(grids[i]);
     p.slot_bytes = p.n * sizeof(float);
     p.capacity = (int64_t)(hbm_budget_bytes / p.slot_bytes);
     if (p.capacity < 1) {

@@ -294,4 +294,66 @@ boltz_status build_tables(boltz_grid_s* g) {
   return BOLTZ_OK;
 }
 
+// Two dimensions, Maxwell molecules (Sec. 3.3, dimension two; Eq. dfor0): Btilde is the
+// constant 2 C_gamma (Eq. Btilde with d_v = 2, gamma = 0), angles theta_p = pi p / A with
+// weight pi / A, alpha_p(k) = Btilde phi2(xi_k . e_p), alpha'_p(k) = phi2(xi_k . e_p-perp)
+// with phi2(s) = int_{-R}^{R} e^{i rho s} d rho = 2 R Sinc(R s); D = sum_p w_p alpha_p
+// alpha'_p.  Tables in (kx, ky) FFT storage order.  The projection uses the invariants
+// (1, v_x, v_y, |v|^2/2); its 4x4 inverse sits in the 5x5 slots {0, 1, 2, 4} of G (row and
+// column 3, the absent v_z, are zero).
+boltz_status build_tables2d(boltz_grid_s* g) {
+  const int N = g->N, M = g->M;
+  const size_t n = (size_t)N * N;
+  g->dv = 2.0 * g->L / N;
+  g->S = 2.0 * g->L / (3.0 + std::sqrt(2.0));
+  if (!(g->R > 0)) g->R = 2.0 * g->S;
+  const double R = g->R;
+  const double bt = 2.0 * g->C_gamma;
+  g->rank = 1;
+  g->M_eff = M;
+  g->e.assign((size_t)M * 3, 0.0);
+  g->wdir.assign(M, kPi / M);
+  g->w.assign(M, kPi / M);
+  try {
+    g->alpha.assign((size_t)M * n, 0.0);
+    g->alphap.assign((size_t)M * n, 0.0);
+    g->D.assign(n, 0.0);
+  } catch (...) {
+    set_error("host allocation of the kernel tables failed");
+    return BOLTZ_ENOMEM;
+  }
+  std::vector<double> xi(N);
+  for (int i = 0; i < N; ++i) xi[i] = kPi * (i < N / 2 ? i : i - N) / g->L;
+  for (int p = 0; p < M; ++p) {
+    const double th = kPi * p / M, c = std::cos(th), sn = std::sin(th);
+    g->e[3 * p + 0] = c;
+    g->e[3 * p + 1] = sn;
+    double* al = &g->alpha[(size_t)p * n];
+    double* ap = &g->alphap[(size_t)p * n];
+    for (int a = 0; a < N; ++a)
+      for (int b = 0; b < N; ++b) {
+        const size_t idx = (size_t)a * N + b;
+        al[idx] = bt * 2.0 * R * sinc(R * (xi[a] * c + xi[b] * sn));
+        ap[idx] = 2.0 * R * sinc(R * (-xi[a] * sn + xi[b] * c));
+      }
+  }
+  for (int p = 0; p < M; ++p)
+    for (size_t k = 0; k < n; ++k) g->D[k] += g->w[p] * g->alpha[(size_t)p * n + k] * g->alphap[(size_t)p * n + k];
+  double A[25] = {0};
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      const double vx = -g->L + a * g->dv, vy = -g->L + b * g->dv;
+      const double phi[5] = {1.0, vx, vy, 0.0, 0.5 * (vx * vx + vy * vy)};
+      for (int r = 0; r < 5; ++r)
+        for (int q = 0; q < 5; ++q) A[r * 5 + q] += phi[r] * phi[q];
+    }
+  A[3 * 5 + 3] = 1.0;  // placeholder for the absent v_z row; removed from G below
+  if (invert5(A, g->proj.G) != 0) {
+    set_error("singular projection matrix");
+    return BOLTZ_EINVAL;
+  }
+  g->proj.G[3 * 5 + 3] = 0.0;
+  return BOLTZ_OK;
+}
+
 }  // namespace boltz

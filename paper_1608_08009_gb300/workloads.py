@@ -11,6 +11,8 @@ Workloads (paper arxiv 1608.08009):
   * two_gaussians_test13 -- the hard-sphere relaxation datum of Test 1.3 (Sec. 5):
     two Gaussians of variance 0.2 centred at +-(-1, -1, -0.25), total mass 1.
   * bkw -- the 3D BKW datum for Maxwell molecules at shape parameter K (rho = 1, T = 1).
+  * two_maxwellians_2d -- the two-Maxwellian cells in two velocity dimensions (the 2D
+    Maxwell-molecule grids of Sec. 3.3).
 """
 
 from __future__ import annotations
@@ -55,6 +57,24 @@ def two_maxwellians(n_cells: int, N: int, L: float, seed: int, cells=None, dtype
     out = np.empty((len(idx), N, N, N), dtype=dtype)
     for o, c in enumerate(idx):
         out[o] = _maxwellian(v, rho[c, 0], u[c, 0], T[c, 0]) + _maxwellian(v, rho[c, 1], u[c, 1], T[c, 1])
+    return out
+
+
+def two_maxwellians_2d(n_cells: int, N: int, L: float, seed: int, cells=None, dtype=np.float64) -> np.ndarray:
+    """2D cells f[c, x, y]: the sum of two 2D Maxwellians per cell with the parameters of
+    two_maxwellians (density U[0.5, 2], drift N(0, 0.3^2) per component, temperature
+    U[0.5, 1.5]; the third drift component is unused)."""
+    rho, u, T = two_maxwellian_params(n_cells, seed)
+    v = velocity_axis(N, L)
+    VX, VY = v[:, None], v[None, :]
+    idx = list(range(n_cells) if cells is None else cells)
+    out = np.empty((len(idx), N, N), dtype=dtype)
+    for o, c in enumerate(idx):
+        f = 0.0
+        for i in range(2):
+            f = f + rho[c, i] / (2.0 * math.pi * T[c, i]) * np.exp(
+                -((VX - u[c, i, 0]) ** 2 + (VY - u[c, i, 1]) ** 2) / (2.0 * T[c, i]))
+        out[o] = f
     return out
 
 
