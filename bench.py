@@ -82,6 +82,7 @@ def make_inputs(wl: dict, cells, total: int):
     return W.two_maxwellians(total, wl["N"], wl["L"], wl["seed"], cells=cells)
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor), nominal
+TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-core rate ratio
 # DRAM bytes (read + write) per cell of one collide_kernel launch, from one ncu capture of
 # the current kernels on a smaller batch of the same workload (traffic grows with the
 # number of cells): profiles/collide_fp32_n32_2048cells.md and
@@ -489,7 +490,9 @@ def run_ours(args, wl):
         dist.init_process_group("nccl")
     B.lib()
     N, L, M, cells = wl["N"], wl["L"], wl["M"], wl["cells"]
-    prec = B.BOLTZ_FP64 if wl["prec"] == "fp64" else B.BOLTZ_FP32_FFT
+    prec = {"fp64": B.BOLTZ_FP64, "fp32_fft": B.BOLTZ_FP32_FFT, "tf32_dft": B.BOLTZ_TF32_DFT,
+            "3xtf32_dft": B.BOLTZ_3XTF32_DFT}[wl["prec"]]
+    tc_split = {"tf32_dft": 1, "3xtf32_dft": 3}.get(wl["prec"], 0)
     dtype = torch.float64 if wl["f64"] else torch.float32
     dim = wl.get("dim", 3)
     if dim == 2:
@@ -622,24 +625,36 @@ def run_ours(args, wl):
         flops_cell = algorithmic_flops(N, grid.info["M_eff"], dim)
         avg_s = statistics.mean(step_ms) / 1000.0 / rk  # one launch per collision evaluation
         achieved = flops_cell * cells / avg_s / 1e12
+        bound = "alu"
         if wl["prec"] == "fp64":
             peak, peak_note = NOMINAL_FP64_TFLOPS, "nominal FP64 ALU 1.25 TFLOP/s"
+        elif tc_split:
+            # executed tensor FLOPs: every inverse 1D pass of every term is a dense
+            # [N^2 pencils x 2N] x [2N x 2N] real contraction per cell (x3 for 3xTF32)
+            bound = "tensor"
+            sust = peaks.get("bf16_tflops_sustained") or 1700.0
+            peak = sust * TF32_PER_BF16
+            peak_note = "measured sustained bf16 %.1f TFLOP/s x nominal tf32/bf16 ratio 1.1/2.25 (of measured)" % sust
+            achieved = ((grid.info["M_eff"] + 1) * 3 * N ** 2 * (2 * N) ** 2 * 2.0 * tc_split * cells
+                        / avg_s / 1e12)
         else:
             peak, peak_note = NOMINAL_FP32_TFLOPS, "FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz"
         line = {
             "metric": "cell-collisions/s", "value": value, "unit": "cell-collisions/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if wl["prec"] == "fp64" else "f32", "data": "synthetic",
+            "dtype": {"fp64": "f64", "tf32_dft": "tf32", "3xtf32_dft": "3xtf32"}.get(wl["prec"], "f32"),
+            "data": "synthetic",
             "config": config_of(args, wl),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
                          "traffic": ((NCU_DRAM_BYTES_PER_CELL.get(wl["prec"]) or 0) * cells or None) if dim == 3
                          and N == 32 else None,
                          "traffic_unit": "bytes per launch (ncu dram read+write, scaled by cells)",
                          "algorithmic_bytes": 2 * N ** dim * (8 if wl["f64"] else 4) * cells,
                          "kernel": "collide_kernel (one launch per step)",
-                         "flops_per_cell": flops_cell, "peak_source": peak_note},
+                         "flops_per_cell": flops_cell, "peak_source": peak_note,
+                         "fft_equivalent_tflops": flops_cell * cells / avg_s / 1e12},
             "e2e": {"value": e2e_value, "unit": "cell-collisions/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": args.steps * rk,
@@ -681,6 +696,8 @@ def main():
                     help="term groups of the serving grids, e.g. 16:4,32:8 (default)")
     ap.add_argument("--term-groups", type=int, default=0, help="override the workload grid's term_groups")
     ap.add_argument("--cluster-size", type=int, default=0, help="override the float32 cluster size")
+    ap.add_argument("--prec", default="", choices=["", "fp32_fft", "tf32_dft", "3xtf32_dft", "fp64"],
+                    help="override the workload's precision mode")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.cells > 0:
@@ -689,6 +706,9 @@ def main():
         wl["opts"] = dict(wl.get("opts", {}), term_groups=args.term_groups)
     if args.cluster_size > 0:
         wl["opts"] = dict(wl.get("opts", {}), cluster_size=args.cluster_size)
+    if args.prec:
+        wl["prec"] = args.prec
+        wl["f64"] = args.prec == "fp64"
     args.serve_groups = ({int(a): int(b) for a, b in (kv.split(":") for kv in args.serve_groups.split(","))}
                          if args.serve_groups else None)
     if args.impl == "reference":

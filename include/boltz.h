@@ -57,9 +57,13 @@ typedef enum {
 typedef enum {
   BOLTZ_FP64 = 0,          /* float64 register FFTs on CUDA cores (the plain form)      */
   BOLTZ_FP32_FFT = 1,      /* float32 register FFTs on CUDA cores, float32 tables       */
-  BOLTZ_TF32_DFT = 2,      /* reserved: tensor-core dense DFT contractions              */
-  BOLTZ_3XBF16_DFT = 3,    /* reserved                                                  */
-  BOLTZ_3XTF32_DFT = 4     /* reserved                                                  */
+  BOLTZ_TF32_DFT = 2,      /* every inverse 1D pass of the term loop as a dense DFT
+                              contraction on the tensor cores (tcgen05, kind::tf32, f32
+                              accumulate in TMEM); inputs rounded to tf32 (~1e-3 relative
+                              per pass).  N = 16, 32; reduced-precision comparison mode  */
+  BOLTZ_3XBF16_DFT = 3,    /* reserved (returns BOLTZ_EUNSUPPORTED)                     */
+  BOLTZ_3XTF32_DFT = 4     /* as BOLTZ_TF32_DFT with operands split into tf32 high and
+                              low parts, Ah Wh + Ah Wl + Al Wh: float32-class accuracy  */
 } boltz_precision;
 
 /* Options of boltz_create_grid.  Pass NULL for all defaults; boltz_default_opts()

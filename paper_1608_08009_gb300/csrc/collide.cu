@@ -76,8 +76,12 @@ struct CollideArgs {
 // Status bits of g_boltz_status.
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusBadIndex = 4u;
+constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on a tensor-core barrier gave up
 
-template <typename T, int N, int C>
+// Tensor-core transform modes of the float32 path (0: register FFT).
+constexpr int kTcNone = 0, kTcTF32 = 1, kTc3xTF32 = 3;
+
+template <typename T, int N, int C, int TC = kTcNone>
 struct CollideCfg {
   static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
   static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
@@ -85,14 +89,15 @@ struct CollideCfg {
   // CTAs per SM asked of the register allocator.  float32 32^3 with C = 8: 3 (168
   // registers, 44 bytes spilled outside the term loop) runs 11 % faster on GB300 than the
   // 252-register 2-CTA version: twelve warps hide the table loads and barrier waits.
-  static constexpr int MIN_BLOCKS = (sizeof(T) == 4 && N == 32 && C == 8) ? 3 : 1;
+  static constexpr int MIN_BLOCKS =
+      (TC == kTcTF32) ? 2 : (TC == kTc3xTF32) ? 1 : (sizeof(T) == 4 && N == 32 && C == 8) ? 3 : 1;
   using T2 = typename Vec2<T>::type;
   static constexpr bool kF32 = sizeof(T) == 4;
   // float32: the spectrum pencil of each thread stays in registers and the x-plane
   // buffer is double-buffered (one cluster barrier per direction); float64 (register
   // bound) keeps the spectrum in shared memory with a single x-plane buffer.
   static constexpr bool kRegSpec = kF32;
-  static constexpr int NXB = kRegSpec ? 2 : 1;
+  static constexpr int NXB = (kRegSpec && TC == kTcNone) ? 2 : 1;
   // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
   // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
   // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
@@ -109,7 +114,18 @@ struct CollideCfg {
   // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA; then
   // the last-arrival flag of split launches
   static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
-  static constexpr size_t SMEM = OFF_FLAG + 16;
+  // tensor-core transforms: operand tiles (rows of 2N floats, K-major without swizzle:
+  // 8-row x 16-byte core matrices, K-adjacent ones 128 bytes apart), the DFT matrix,
+  // the MMA-completion barrier and the TMEM address
+  static constexpr int TC_K = 2 * N;
+  static constexpr int TC_SPLIT = (TC == kTc3xTF32) ? 2 : 1;
+  static constexpr size_t OFF_TCA = (OFF_FLAG + 16 + 1023) / 1024 * 1024;
+  static constexpr size_t TCA_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * THREADS * TC_K * 4 : 0;
+  static constexpr size_t OFF_TCW = OFF_TCA + TCA_BYTES;
+  static constexpr size_t TCW_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * TC_K * TC_K * 4 : 0;
+  static constexpr size_t OFF_TCB = OFF_TCW + TCW_BYTES;  // mbarrier (8 B) + TMEM address (4 B)
+  static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 16;
+  static_assert(TC == kTcNone || (kF32 && THREADS == 128), "tensor-core transforms: float32, 128 pencils per CTA");
   static_assert(THREADS % 32 == 0, "whole warps");
   static_assert(NP % VEC == 0, "whole chunks");
   static_assert(OFF_XB % 16 == 0 && (XB * sizeof(T2)) % 16 == 0, "16-byte aligned buffers");
@@ -241,10 +257,143 @@ __device__ __forceinline__ void cluster_correction(const CollideArgs& args, cons
   cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
 }
 
-template <typename T, typename TIO, int N, int C, bool kSplit>
-__global__ void __launch_bounds__(CollideCfg<T, N, C>::THREADS, CollideCfg<T, N, C>::MIN_BLOCKS)
+// ---- tensor-core 1D DFT of 128 pencils (tcgen05, kind::tf32) --------------------------
+// Each thread of the CTA holds one pencil of N complex values.  The inverse DFT of all
+// 128 pencils is one dense contraction D[128 x 2N] = A[128 x 2N] W[2N x 2N] with the real
+// block form A = [re | im], W = [[C, S], [-S, C]] (C, S = cos, sin of 2 pi x k / N): rows
+// go to shared memory, one thread issues the MMAs (accumulator in TMEM), the others wait
+// on an mbarrier with a bounded number of tries, and every thread reads its row back
+// with tcgen05.ld.  3xTF32 splits A and W into tf32 high and low parts and accumulates
+// Ah Wh + Ah Wl + Al Wh (the Al Wl term is below float32 rounding).
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// float index of element (row, k) of a K-major, no-swizzle tile with K columns
+template <int K>
+__device__ __forceinline__ int kmajor(int row, int k) {
+  return (row / 8) * (K * 8) + (k / 4) * 32 + (row % 8) * 4 + (k % 4);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+template <int N, int TC>
+struct TcDft {
+  static constexpr int K = 2 * N;
+  float* A;           // [TC_SPLIT][128 x K]
+  const float* W;     // [TC_SPLIT][K x K] as B operand rows n (output), K-major
+  uint64_t* mbar;
+  uint32_t tmem;
+  uint32_t phase;
+
+  // the inverse-DFT matrix from the twiddle table, high and low tf32 parts
+  __device__ static void build_w(float* Wdst, int t, int nthreads) {
+    constexpr int stride = kTw / N;
+    for (int i = t; i < K * K; i += nthreads) {
+      const int nn = i / K, k = i % K;  // output index, input index
+      const int x = nn % N, kk = k % N;
+      const int m = (x * kk) % N;
+      const float c = tw_cos<float>(m * stride), sn = tw_sin<float>(m * stride);
+      float v;
+      if (nn < N) v = (k < N) ? c : -sn;   // Re y = C Re a - S Im a
+      else v = (k < N) ? sn : c;           // Im y = S Re a + C Im a
+      const float hi = to_tf32(v);
+      Wdst[kmajor<K>(nn, k)] = hi;
+      if (TC == kTc3xTF32) Wdst[K * K + kmajor<K>(nn, k)] = to_tf32(v - hi);
+    }
+  }
+
+  __device__ __forceinline__ void mma_set(uint32_t a_addr, uint32_t b_addr, bool first) const {
+    // D f32, A and B tf32, both K-major, N = K, M = 128
+    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K >> 3) << 17) | ((128u >> 4) << 24);
+#pragma unroll
+    for (int s = 0; s < K / 8; ++s) {
+      const uint64_t ad = umma_desc(a_addr + s * 256, 128, K * 32);
+      const uint64_t bd = umma_desc(b_addr + s * 256, 128, K * 32);
+      const uint32_t acc = (first && s == 0) ? 0u : 1u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+  }
+
+  // inverse DFT of this thread's pencil (re, im) in place; all 128 threads call it
+  __device__ __forceinline__ void inverse(float (&re)[N], float (&im)[N], int t) {
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+      const float4 hr = make_float4(to_tf32(re[k]), to_tf32(re[k + 1]), to_tf32(re[k + 2]), to_tf32(re[k + 3]));
+      const float4 hi = make_float4(to_tf32(im[k]), to_tf32(im[k + 1]), to_tf32(im[k + 2]), to_tf32(im[k + 3]));
+      *reinterpret_cast<float4*>(A + kmajor<K>(t, k)) = hr;
+      *reinterpret_cast<float4*>(A + kmajor<K>(t, N + k)) = hi;
+      if constexpr (TC == kTc3xTF32) {
+        float* Al = A + 128 * K;
+        *reinterpret_cast<float4*>(Al + kmajor<K>(t, k)) =
+            make_float4(to_tf32(re[k] - hr.x), to_tf32(re[k + 1] - hr.y), to_tf32(re[k + 2] - hr.z),
+                        to_tf32(re[k + 3] - hr.w));
+        *reinterpret_cast<float4*>(Al + kmajor<K>(t, N + k)) =
+            make_float4(to_tf32(im[k] - hi.x), to_tf32(im[k + 1] - hi.y), to_tf32(im[k + 2] - hi.z),
+                        to_tf32(im[k + 3] - hi.w));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+      const uint32_t a0 = smem_u32(A), w0 = smem_u32(W);
+      mma_set(a0, w0, true);
+      if constexpr (TC == kTc3xTF32) {
+        mma_set(a0, w0 + K * K * 4, false);        // Ah Wl
+        mma_set(a0 + 128 * K * 4, w0, false);      // Al Wh
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; ++it) {
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(mbar)), "r"(phase)
+          : "memory");
+    }
+    if (!done) atomicOr(&g_boltz_status, kStatusTimeout);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t lane_base = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+#pragma unroll
+    for (int c = 0; c < K; c += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(lane_base + c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c + j;
+        if (col < N) re[col] = __uint_as_float(r[j]);
+        else im[col - N] = __uint_as_float(r[j]);
+      }
+    }
+  }
+};
+
+template <typename T, typename TIO, int N, int C, bool kSplit, int TC = kTcNone>
+__global__ void __launch_bounds__(CollideCfg<T, N, C, TC>::THREADS, CollideCfg<T, N, C, TC>::MIN_BLOCKS)
 collide_kernel(const CollideArgs args) {
-  using Cfg = CollideCfg<T, N, C>;
+  using Cfg = CollideCfg<T, N, C, TC>;
+  static_assert(!(kSplit && TC != kTcNone), "tensor-core transforms run without term groups");
   using T2 = typename Cfg::T2;
   constexpr int NP = Cfg::NP, WARPS = Cfg::WARPS, VEC = Cfg::VEC, NCH = Cfg::NCH, RW_ = Cfg::RW;
   constexpr int n = N * N * N;
@@ -289,6 +438,39 @@ collide_kernel(const CollideArgs args) {
 
   T re[N], im[N];
   T fr[kRegSpec ? N : 1], fi[kRegSpec ? N : 1];  // spectrum pencil (kRegSpec)
+
+  // tensor-core transforms: TMEM accumulator (2N columns), completion barrier, DFT matrix
+  TcDft<N, TC> tc;
+  if constexpr (TC != kTcNone) {
+    tc.A = reinterpret_cast<float*>(smem_raw + Cfg::OFF_TCA);
+    tc.W = reinterpret_cast<const float*>(smem_raw + Cfg::OFF_TCW);
+    tc.mbar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::OFF_TCB);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TCB + 8);
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(2 * N));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tc.mbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    TcDft<N, TC>::build_w(reinterpret_cast<float*>(smem_raw + Cfg::OFF_TCW), threadIdx.x, Cfg::THREADS);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc.tmem = *tmem_slot;
+    tc.phase = 0u;
+  }
+  // inverse 1D transform of this thread's pencil: register FFT or tensor-core DFT
+  auto inverse_1d = [&]() {
+    if constexpr (TC != kTcNone) {
+      tc.inverse(re, im, threadIdx.x);
+    } else {
+      fft_regs<N, +1>(re, im);
+    }
+  };
 
   const double L = args.geom.L, dv = args.geom.dv;
   const int lane = t & 31, warp = t >> 5;
@@ -372,7 +554,7 @@ collide_kernel(const CollideArgs args) {
       }
     }
   }
-  if constexpr (!kRegSpec) cluster_barrier<C>();  // single buffer: peers done reading it
+  if constexpr (Cfg::NXB == 1) cluster_barrier<C>();  // single buffer: peers done reading it
 
   // ---- angular loop: one complex inverse transform per separated term --------------
   T acc[N];
@@ -395,7 +577,7 @@ collide_kernel(const CollideArgs args) {
       re[kx] = ab.x * c.x - ab.y * c.y;
       im[kx] = ab.x * c.y + ab.y * c.x;
     }
-    fft_regs<N, +1>(re, im);
+    inverse_1d();
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
       T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
@@ -417,7 +599,7 @@ collide_kernel(const CollideArgs args) {
       re[kz] = v.x;
       im[kz] = v.y;
     }
-    fft_regs<N, +1>(re, im);
+    inverse_1d();
 #pragma unroll
     for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
   };
@@ -431,7 +613,7 @@ collide_kernel(const CollideArgs args) {
       re[ky] = v.x;
       im[ky] = v.y;
     }
-    fft_regs<N, +1>(re, im);
+    inverse_1d();
     if (accumulate) {
 #pragma unroll
       for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
@@ -444,7 +626,7 @@ collide_kernel(const CollideArgs args) {
   const int j1 = kSplit ? (int)(((long long)(gi + 1) * M_eff) / G) : M_eff;
   const bool has_loss = kSplit ? (gi == G - 1) : true;
   const int nt = (j1 - j0) + (has_loss ? 1 : 0);
-  if constexpr (kRegSpec) {
+  if constexpr (Cfg::NXB == 2) {
     // Two x-plane buffers; term i uses buffer (i + 1) % 2.  The ky pass of term i - 1
     // runs between the scatter of term i and the cluster barrier, so the remote stores
     // drain behind it.  It reads the other buffer, and every CTA finishes it before
@@ -480,6 +662,13 @@ collide_kernel(const CollideArgs args) {
     }
   }
 
+  if constexpr (TC != kTcNone) {
+    // every thread has read its last accumulator row: free the TMEM columns
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(2 * N));
+  }
   if constexpr (kSplit) {
     // Partial gain (and the loss multiplier) of this group, then the last-arrival count
     // of the cell (fence, barrier, one atomic: no waiting).  The cluster that arrives last
@@ -1180,11 +1369,16 @@ boltz_status upload_tables(boltz_grid_s* g) {
   return BOLTZ_OK;
 }
 
-template <typename T, typename TIO, int N, int C>
+template <typename T, typename TIO, int N, int C, int TC = kTcNone>
 static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
-  using Cfg = CollideCfg<T, N, C>;
+  using Cfg = CollideCfg<T, N, C, TC>;
   const bool split = a.groups > 1;
-  auto kern = split ? collide_kernel<T, TIO, N, C, true> : collide_kernel<T, TIO, N, C, false>;
+  void (*kern)(const CollideArgs);
+  if constexpr (TC != kTcNone) {
+    kern = collide_kernel<T, TIO, N, C, false, TC>;  // no term groups with tensor-core transforms
+  } else {
+    kern = split ? collide_kernel<T, TIO, N, C, true> : collide_kernel<T, TIO, N, C, false>;
+  }
   // function attributes are per device: set them once per (instantiation, device), and
   // check once that a cluster of this size can be scheduled at all
   static std::atomic<unsigned long long> prepared[2], unschedulable[2];
@@ -1331,7 +1525,18 @@ bool collide_supported_grid(const boltz_grid_s* g, int prec) {
   return collide_supported(g->N, prec);
 }
 
+// Tensor-core transforms (BOLTZ_TF32_DFT, BOLTZ_3XTF32_DFT): 128 pencils per CTA, i.e.
+// N = 32 with clusters of 8 and N = 16 with clusters of 2.
+template <typename TIO, int TC>
+static boltz_status dispatch_tc(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  if (g->N == 32) return launch_impl<float, TIO, 32, 8, TC>(a, n_cells, st);
+  if (g->N == 16) return launch_impl<float, TIO, 16, 2, TC>(a, n_cells, st);
+  set_error("no tensor-core kernel for this N");
+  return BOLTZ_EUNSUPPORTED;
+}
+
 bool collide_supported(int N, int prec) {
+  if (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XTF32_DFT) return N == 16 || N == 32;
   if (N == 8 || N == 16 || N == 24 || N == 32) return prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT;
   if (N == 48 || N == 64) return prec == BOLTZ_FP32_FFT;  // float64 pencils of 48/64 do not fit
   return false;
@@ -1465,7 +1670,8 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                      : dispatch2d<float, float>(g, a2, n_cells, stream);
   }
   if (cluster == 0 && prec != BOLTZ_FP64) cluster = g->cluster_size;  // 0: the default of (N, prec)
-  int G = groups < 0 ? g->term_groups : groups;
+  const bool tc = (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XTF32_DFT);
+  int G = tc ? 1 : (groups < 0 ? g->term_groups : groups);
   G = std::max(1, std::min(G, g->M_eff));
   if (n_cells * (int64_t)G * 16 > (int64_t)INT32_MAX) {
     set_error("n_cells * term_groups too large for one launch");
@@ -1524,6 +1730,12 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                      : dispatch_n<double, float>(g, args, n_cells, stream, cluster);
   }
   args.tab = g->tab32;
+  if (prec == BOLTZ_TF32_DFT)
+    return f_is_fp64 ? dispatch_tc<double, kTcTF32>(g, args, n_cells, stream)
+                     : dispatch_tc<float, kTcTF32>(g, args, n_cells, stream);
+  if (prec == BOLTZ_3XTF32_DFT)
+    return f_is_fp64 ? dispatch_tc<double, kTc3xTF32>(g, args, n_cells, stream)
+                     : dispatch_tc<float, kTc3xTF32>(g, args, n_cells, stream);
   return f_is_fp64 ? dispatch_n<float, double>(g, args, n_cells, stream, cluster)
                    : dispatch_n<float, float>(g, args, n_cells, stream, cluster);
 }

@@ -401,3 +401,36 @@ def test_large_grids_parity(N, L, M, groups):
             B.boltz_collide(g.batch(cells, B.BOLTZ_FP64, True), torch.from_numpy(f).cuda(),
                             torch.empty(cells, N, N, N, dtype=torch.float64, device="cuda"))
         assert ei.value.status == B.BOLTZ_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("N,L,M", [(16, 6.0, 16), (32, 8.0, 16)])
+def test_tensor_core_dft_modes(N, L, M):
+    """Inverse 1D passes as dense DFT contractions on the tensor cores.  3xTF32 (split
+    operands) is float32-class: within twice the float32 bound (a direct N-term DFT sum
+    accumulates sqrt(N) eps32 where the FFT accumulates log2(N) eps32).  TF32 rounds every
+    pass input to 11 significant bits: relative error per pass <= 2^-11 after rounding of
+    both operands, three passes, amplified by kappa like the float32 error."""
+    cells = 3
+    f = W.two_maxwellians(cells, N, L, seed=131)
+    og = oracle_grid(N, L, M)
+    Qref = O.collide(f, og)
+    Qp, Lo = O.operator.gain_loss(f, og)
+    kappa = np.linalg.norm(Qp) / np.linalg.norm(Qp - f * Lo)
+    with B.Grid(N, L, 1.0, M) as g:
+        e3 = rel_l2(run_collide(g, f, B.BOLTZ_3XTF32_DFT, fp64=False), Qref)
+        e1 = rel_l2(run_collide(g, f, B.BOLTZ_TF32_DFT, fp64=False), Qref)
+        print(f"N={N}: 3xTF32 {e3:.3e}  TF32 {e1:.3e}  fp32 bound {fp32_tol(f, og):.3e}  kappa {kappa:.1f}")
+        assert e3 <= 2.0 * fp32_tol(f, og)
+        assert e1 <= 3.0 * 2.0 ** -11 * kappa
+        assert e1 > e3
+        # relax with a tensor-core mode keeps the moments (float64 projection)
+        ft = torch.from_numpy(f).float().cuda()
+        B.boltz_relax(g.batch(cells, B.BOLTZ_3XTF32_DFT, False), ft, 0.004, 2)
+        B.boltz_stream_status()
+        U0 = O.moments(f.astype(np.float32).astype(np.float64), og)
+        U1 = O.moments(ft.double().cpu().numpy(), og)
+        assert np.max(np.abs(U1 - U0) / np.abs(U0).max(axis=1, keepdims=True)) < 1e-6
+    with B.Grid(24, 7.0, 1.0, 8) as g:
+        with pytest.raises(B.BoltzError) as ei:
+            run_collide(g, W.two_maxwellians(1, 24, 7.0, seed=1), B.BOLTZ_TF32_DFT, fp64=False)
+        assert ei.value.status == B.BOLTZ_EUNSUPPORTED
