@@ -1,5 +1,5 @@
 // C ABI of libboltz (declared in include/boltz.h): argument checking, grid ownership,
-// relaxation driver.  All compute happens in the kernels of collide.cu.
+// relaxation driver.  All compute happens in the kernels of the collide*.cu units.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -1,0 +1,1357 @@
+#pragma once
+// Device code of the fused per-cell kernels of the fast spectral collision operator
+// (sm_103a), shared by the kernel translation units collide_f32.cu, collide_f64.cu,
+// collide_tc.cu and collide_2d.cu.
+//
+// Paper: arxiv 1608.08009.  Per cell (Sec. 4.2): one forward 3D transform of f
+// (Eq. FC), then for every separated quadrature term j the coefficients
+// (alpha_j + i alpha'_j) fhat and one inverse 3D transform (Eq. FU) whose real and
+// imaginary parts are the two factors of the gain term (Sec. 3.3, decoupling formula),
+// accumulated as Q+ += w_j Re Im; then the loss term L = inverse(D fhat), Q = Q+ - f L,
+// the conservation projection (Sec. 3.2, Eq. minim1) and optionally the collision step
+// f <- f + dt Q (Eq. f_coll), all in one launch: f is read once and Q (or the new f)
+// written once per cell.
+//
+// Work decomposition.  A cell is owned by a thread-block cluster of C CTAs.
+//  * Spectrum: CTA c keeps fhat(kx, ky, kz) for the ky-slab [c N/C, (c+1) N/C), all kx
+//    and kz: in registers (float32, thread (ky, kz) holds its kx pencil) or shared memory.
+//  * Physical space: CTA q owns the x-slab [q N/C, (q+1) N/C); the gain accumulator of
+//    its points lives in registers (thread (x, z) holds the N values along y).
+//  * One inverse 3D transform = pass along kx (pencils of the CTA's ky-slab, in
+//    registers) whose N outputs are scattered by x into the owners' shared memory through
+//    distributed shared memory, a cluster barrier, then the passes along kz and ky inside
+//    each x-plane of the owner.
+//  * Every 1D pass is a fully unrolled radix-4/2 FFT of one pencil held by one thread.
+// Twiddles, kernel tables and weights are float32 for the BOLTZ_FP32_FFT path and
+// float64 for BOLTZ_FP64.  Moments, projection and the update are float64 in both.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <string>
+
+#include "fft_regs.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace boltz {
+
+// Device status word of this translation unit (each unit has its own copy; the host
+// reads and clears all of them): bit 0 non-finite output, bit 2 bad cell index, bit 3
+// a bounded tensor-core wait gave up.
+static __device__ unsigned int g_boltz_status;
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T> __device__ __forceinline__ typename Vec2<T>::type mk2(T a, T b);
+template <> __device__ __forceinline__ float2 mk2<float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ double2 mk2<double>(double a, double b) { return make_double2(a, b); }
+
+// CollideArgs (internal.h) is the argument block of every collision kernel.
+
+
+// Status bits of g_boltz_status.
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusBadIndex = 4u;
+constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on a tensor-core barrier gave up
+
+// Tensor-core transform modes of the float32 path (0: register FFT).
+constexpr int kTcNone = 0, kTcTF32 = 1, kTc3xTF32 = 3;
+
+template <typename T, int N, int C, int TC = kTcNone>
+struct CollideCfg {
+  static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
+  static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
+  static constexpr int WARPS = THREADS / 32;
+  // CTAs per SM asked of the register allocator.  float32 32^3 with C = 8: 3 (168
+  // registers, 44 bytes spilled outside the term loop) runs 11 % faster on GB300 than the
+  // 252-register 2-CTA version: twelve warps hide the table loads and barrier waits.
+  static constexpr int MIN_BLOCKS =
+      (TC == kTcTF32) ? 2 : (TC == kTc3xTF32) ? 1 : (sizeof(T) == 4 && N == 32 && C == 8) ? 3 : 1;
+  using T2 = typename Vec2<T>::type;
+  static constexpr bool kF32 = sizeof(T) == 4;
+  // float32: the spectrum pencil of each thread stays in registers and the x-plane
+  // buffer is double-buffered (one cluster barrier per direction); float64 (register
+  // bound) keeps the spectrum in shared memory with a single x-plane buffer.
+  static constexpr bool kRegSpec = kF32;
+  static constexpr int NXB = (kRegSpec && TC == kTcNone) ? 2 : 1;
+  // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
+  // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
+  // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
+  // kz) then stores 32 contiguous 16-byte chunks to a peer: full 32-byte sectors on the
+  // SM-to-SM network.  RW = N + 1 (odd) keeps the in-plane passes conflict-free with lanes
+  // ordered (x % VEC, ky) and (x % VEC, z).
+  static constexpr int VEC = kF32 ? 2 : 1;
+  static constexpr int NCH = NP / VEC;  // chunks per (ky, k)
+  static constexpr int RW = N + 1;
+  static constexpr size_t FH = kRegSpec ? 0 : (size_t)N * NP * N;  // spectrum slab [kx][kyl][kz]
+  static constexpr size_t XB = (size_t)NCH * N * RW * VEC;
+  static constexpr size_t OFF_XB = FH * sizeof(T2);
+  static constexpr size_t OFF_RED = OFF_XB + NXB * XB * sizeof(T2);
+  // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA; then
+  // the last-arrival flag of split launches
+  static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  // tensor-core transforms: operand tiles (rows of 2N floats, K-major without swizzle:
+  // 8-row x 16-byte core matrices, K-adjacent ones 128 bytes apart), the DFT matrix,
+  // the MMA-completion barrier and the TMEM address
+  static constexpr int TC_K = 2 * N;
+  static constexpr int TC_SPLIT = (TC == kTc3xTF32) ? 2 : 1;
+  static constexpr size_t OFF_TCA = (OFF_FLAG + 16 + 1023) / 1024 * 1024;
+  static constexpr size_t TCA_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * THREADS * TC_K * 4 : 0;
+  static constexpr size_t OFF_TCW = OFF_TCA + TCA_BYTES;
+  static constexpr size_t TCW_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * TC_K * TC_K * 4 : 0;
+  static constexpr size_t OFF_TCB = OFF_TCW + TCW_BYTES;  // mbarrier (8 B) + TMEM address (4 B)
+  static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 16;
+  static_assert(TC == kTcNone || (kF32 && THREADS == 128), "tensor-core transforms: float32, 128 pencils per CTA");
+  static_assert(THREADS % 32 == 0, "whole warps");
+  static_assert(NP % VEC == 0, "whole chunks");
+  static_assert(OFF_XB % 16 == 0 && (XB * sizeof(T2)) % 16 == 0, "16-byte aligned buffers");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static __device__ __forceinline__ int elem(int xl, int ky, int k) {
+    return ((xl / VEC) * N + ky) * RW * VEC + k * VEC + xl % VEC;
+  }
+};
+
+template <int C>
+__device__ __forceinline__ void cluster_barrier() {
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+template <int C, typename P>
+__device__ __forceinline__ P* cta_smem(P* p, int r) {
+  if constexpr (C > 1) {
+    return cg::this_cluster().map_shared_rank(p, (unsigned)r);
+  } else {
+    return p;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared::cluster address of `addr` (a shared::cta address) in the CTA of rank r
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t r) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(r));
+  return out;
+}
+
+// One 16-byte chunk of the x-plane buffer: two float2 (x, x + 1) or one double2.
+__device__ __forceinline__ void st_cluster_chunk(uint32_t a, const float* re, const float* im) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};"
+               :: "r"(a), "f"(re[0]), "f"(im[0]), "f"(re[1]), "f"(im[1]) : "memory");
+}
+__device__ __forceinline__ void st_cluster_chunk(uint32_t a, const double* re, const double* im) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" :: "r"(a), "d"(re[0]), "d"(im[0]) : "memory");
+}
+__device__ __forceinline__ void ld_cluster_chunk(uint32_t a, float* re, float* im) {
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(re[0]), "=f"(im[0]), "=f"(re[1]), "=f"(im[1]) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ld_cluster_chunk(uint32_t a, double* re, double* im) {
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(re[0]), "=d"(im[0]) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void st_local_chunk(float2* p, const float* re, const float* im) {
+  *reinterpret_cast<float4*>(p) = make_float4(re[0], im[0], re[1], im[1]);
+}
+__device__ __forceinline__ void st_local_chunk(double2* p, const double* re, const double* im) {
+  *p = make_double2(re[0], im[0]);
+}
+__device__ __forceinline__ void ld_local_chunk(const float2* p, float* re, float* im) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  re[0] = v.x; im[0] = v.y; re[1] = v.z; im[1] = v.w;
+}
+__device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, double* im) {
+  const double2 v = *p;
+  re[0] = v.x; im[0] = v.y;
+}
+
+// Projection of Sec. 3.2 (Eq. minim1) for one cell owned by a cluster: m[5] is this
+// thread's share of Phi g; red holds [WARPS][5] scratch, then [5] Phi g and [5] Phi f_in
+// (the targets, when computed) of this CTA.  Returns c5 = G (U - Phi g), zero without
+// projection; U is Phi f_in (compute_targets), Utgt[cell] or zero.  Ends with a cluster
+// barrier, after which no CTA reads a peer's shared memory.
+template <int C, int WARPS>
+__device__ __forceinline__ void cluster_correction(const CollideArgs& args, const double (&m)[5], double* red,
+                                                   long long cell, bool writable, int rank, int t,
+                                                   double (&c5)[5]) {
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const double s = warp_sum(m[r]);
+    if (lane == 0) red[warp * 5 + r] = s;
+  }
+  __syncthreads();
+  if (t < 5) {
+    double s = 0.0;
+    for (int w = 0; w < WARPS; ++w) s += red[w * 5 + t];
+    red[WARPS * 5 + t] = s;  // this CTA's partial sums
+  }
+  cluster_barrier<C>();
+#pragma unroll
+  for (int r = 0; r < 5; ++r) c5[r] = 0.0;
+  if (args.project) {
+    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < C; ++q) {
+      const double* p = cta_smem<C>(red + WARPS * 5, q);
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        tot[r] += p[r];
+        if (args.compute_targets) tgt[r] += p[5 + r];
+      }
+    }
+    if (!args.compute_targets && args.Utgt) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
+    }
+    if (args.compute_targets && args.Utgt && writable && rank == 0) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        if (t == r) args.Utgt[cell * 5 + r] = tgt[r];  // constant register index
+    }
+    double rhs[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) rhs[r] = tgt[r] - tot[r];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += args.geom.G[r * 5 + k] * rhs[k];
+      c5[r] = s;
+    }
+  }
+  cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
+}
+
+// ---- tensor-core 1D DFT of 128 pencils (tcgen05, kind::tf32) --------------------------
+// Each thread of the CTA holds one pencil of N complex values.  The inverse DFT of all
+// 128 pencils is one dense contraction D[128 x 2N] = A[128 x 2N] W[2N x 2N] with the real
+// block form A = [re | im], W = [[C, S], [-S, C]] (C, S = cos, sin of 2 pi x k / N): rows
+// go to shared memory, one thread issues the MMAs (accumulator in TMEM), the others wait
+// on an mbarrier with a bounded number of tries, and every thread reads its row back
+// with tcgen05.ld.  3xTF32 splits A and W into tf32 high and low parts and accumulates
+// Ah Wh + Ah Wl + Al Wh (the Al Wl term is below float32 rounding).
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// float index of element (row, k) of a K-major, no-swizzle tile with K columns
+template <int K>
+__device__ __forceinline__ int kmajor(int row, int k) {
+  return (row / 8) * (K * 8) + (k / 4) * 32 + (row % 8) * 4 + (k % 4);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+template <int N, int TC>
+struct TcDft {
+  static constexpr int K = 2 * N;
+  float* A;           // [TC_SPLIT][128 x K]
+  const float* W;     // [TC_SPLIT][K x K] as B operand rows n (output), K-major
+  uint64_t* mbar;
+  uint32_t tmem;
+  uint32_t phase;
+
+  // the inverse-DFT matrix from the twiddle table, high and low tf32 parts
+  __device__ static void build_w(float* Wdst, int t, int nthreads) {
+    constexpr int stride = kTw / N;
+    for (int i = t; i < K * K; i += nthreads) {
+      const int nn = i / K, k = i % K;  // output index, input index
+      const int x = nn % N, kk = k % N;
+      const int m = (x * kk) % N;
+      const float c = tw_cos<float>(m * stride), sn = tw_sin<float>(m * stride);
+      float v;
+      if (nn < N) v = (k < N) ? c : -sn;   // Re y = C Re a - S Im a
+      else v = (k < N) ? sn : c;           // Im y = S Re a + C Im a
+      const float hi = to_tf32(v);
+      Wdst[kmajor<K>(nn, k)] = hi;
+      if (TC == kTc3xTF32) Wdst[K * K + kmajor<K>(nn, k)] = to_tf32(v - hi);
+    }
+  }
+
+  __device__ __forceinline__ void mma_set(uint32_t a_addr, uint32_t b_addr, bool first) const {
+    // D f32, A and B tf32, both K-major, N = K, M = 128
+    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K >> 3) << 17) | ((128u >> 4) << 24);
+#pragma unroll
+    for (int s = 0; s < K / 8; ++s) {
+      const uint64_t ad = umma_desc(a_addr + s * 256, 128, K * 32);
+      const uint64_t bd = umma_desc(b_addr + s * 256, 128, K * 32);
+      const uint32_t acc = (first && s == 0) ? 0u : 1u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+  }
+
+  // inverse DFT of this thread's pencil (re, im) in place; all 128 threads call it
+  __device__ __forceinline__ void inverse(float (&re)[N], float (&im)[N], int t) {
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+      const float4 hr = make_float4(to_tf32(re[k]), to_tf32(re[k + 1]), to_tf32(re[k + 2]), to_tf32(re[k + 3]));
+      const float4 hi = make_float4(to_tf32(im[k]), to_tf32(im[k + 1]), to_tf32(im[k + 2]), to_tf32(im[k + 3]));
+      *reinterpret_cast<float4*>(A + kmajor<K>(t, k)) = hr;
+      *reinterpret_cast<float4*>(A + kmajor<K>(t, N + k)) = hi;
+      if constexpr (TC == kTc3xTF32) {
+        float* Al = A + 128 * K;
+        *reinterpret_cast<float4*>(Al + kmajor<K>(t, k)) =
+            make_float4(to_tf32(re[k] - hr.x), to_tf32(re[k + 1] - hr.y), to_tf32(re[k + 2] - hr.z),
+                        to_tf32(re[k + 3] - hr.w));
+        *reinterpret_cast<float4*>(Al + kmajor<K>(t, N + k)) =
+            make_float4(to_tf32(im[k] - hi.x), to_tf32(im[k + 1] - hi.y), to_tf32(im[k + 2] - hi.z),
+                        to_tf32(im[k + 3] - hi.w));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+      const uint32_t a0 = smem_u32(A), w0 = smem_u32(W);
+      mma_set(a0, w0, true);
+      if constexpr (TC == kTc3xTF32) {
+        mma_set(a0, w0 + K * K * 4, false);        // Ah Wl
+        mma_set(a0 + 128 * K * 4, w0, false);      // Al Wh
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; ++it) {
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(mbar)), "r"(phase)
+          : "memory");
+    }
+    if (!done) atomicOr(&g_boltz_status, kStatusTimeout);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t lane_base = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+#pragma unroll
+    for (int c = 0; c < K; c += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(lane_base + c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c + j;
+        if (col < N) re[col] = __uint_as_float(r[j]);
+        else im[col - N] = __uint_as_float(r[j]);
+      }
+    }
+  }
+};
+
+template <typename T, typename TIO, int N, int C, bool kSplit, int TC = kTcNone>
+__global__ void __launch_bounds__(CollideCfg<T, N, C, TC>::THREADS, CollideCfg<T, N, C, TC>::MIN_BLOCKS)
+collide_kernel(const CollideArgs args) {
+  using Cfg = CollideCfg<T, N, C, TC>;
+  static_assert(!(kSplit && TC != kTcNone), "tensor-core transforms run without term groups");
+  using T2 = typename Cfg::T2;
+  constexpr int NP = Cfg::NP, WARPS = Cfg::WARPS, VEC = Cfg::VEC, NCH = Cfg::NCH, RW_ = Cfg::RW;
+  constexpr int n = N * N * N;
+  constexpr bool kRegSpec = Cfg::kRegSpec;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T2* Fh = reinterpret_cast<T2*>(smem_raw);                       // unused when kRegSpec
+  T2* XB0 = reinterpret_cast<T2*>(smem_raw + Cfg::OFF_XB);
+  double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
+
+  const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  // Cell of the launch and term group of this cluster.
+  const int G = kSplit ? args.groups : 1;
+  long long lc = blockIdx.x / C;
+  int gi = 0;
+  if constexpr (kSplit) {
+    gi = (int)(lc % G);
+    lc /= G;
+  }
+  // Slot of this cell.  An index outside [0, pool_cells) is reported; the cell then
+  // reads slot 0 and writes nothing, so every CTA still runs the same barrier sequence.
+  long long cell = lc;
+  bool writable = true;
+  if (args.cell_idx) {
+    const long long s = args.cell_idx[cell];
+    writable = (s >= 0 && s < args.pool_cells);
+    if (!writable && threadIdx.x == 0) atomicOr(&g_boltz_status, kStatusBadIndex);
+    cell = writable ? s : 0;
+  }
+  const int t = threadIdx.x;
+  // spectral passes: thread (kyl, kz), lanes along kz
+  const int kyl = t / N, kzt = t % N;
+  // physical passes: thread (xl, ky) in the kz pass, (xl, z) in the ky pass / epilogue,
+  // lanes ordered (xl % VEC, ky or z), xl / VEC slowest
+  const int xlt = (t / (VEC * N)) * VEC + t % VEC, grp = (t / VEC) % N;
+  const int zt = grp;
+  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  const int ky_own = rank * NP + kyl;  // spectral ky of this thread's pencils
+  const int x_own = rank * NP + xlt;   // physical x of this thread's rows
+
+  T re[N], im[N];
+  T fr[kRegSpec ? N : 1], fi[kRegSpec ? N : 1];  // spectrum pencil (kRegSpec)
+
+  // tensor-core transforms: TMEM accumulator (2N columns), completion barrier, DFT matrix
+  TcDft<N, TC> tc;
+  if constexpr (TC != kTcNone) {
+    tc.A = reinterpret_cast<float*>(smem_raw + Cfg::OFF_TCA);
+    tc.W = reinterpret_cast<const float*>(smem_raw + Cfg::OFF_TCW);
+    tc.mbar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::OFF_TCB);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TCB + 8);
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(2 * N));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tc.mbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    TcDft<N, TC>::build_w(reinterpret_cast<float*>(smem_raw + Cfg::OFF_TCW), threadIdx.x, Cfg::THREADS);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc.tmem = *tmem_slot;
+    tc.phase = 0u;
+  }
+  // inverse 1D transform of this thread's pencil: register FFT or tensor-core DFT
+  auto inverse_1d = [&]() {
+    if constexpr (TC != kTcNone) {
+      tc.inverse(re, im, threadIdx.x);
+    } else {
+      fft_regs<N, +1>(re, im);
+    }
+  };
+
+  const double L = args.geom.L, dv = args.geom.dv;
+  const int lane = t & 31, warp = t >> 5;
+  // ---- forward transform, pass along y: thread (x, z) --------------------------------
+  {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // sum_y f, sum_y y f, sum_y y^2 f (targets)
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const TIO fv = fin[(x_own * N + y) * N + zt];
+      re[y] = (T)fv;
+      im[y] = T(0);
+      if (args.compute_targets) {
+        s0 += (double)fv;
+        s1 += (double)y * (double)fv;
+        s2 += (double)(y * y) * (double)fv;
+      }
+    }
+    if (args.compute_targets) {
+      // Phi f over this thread's y-row: v_y = -L + y dv
+      const double vx = -L + x_own * dv, vz = -L + zt * dv;
+      const double sy = -L * s0 + dv * s1;                              // sum v_y f
+      const double syy = L * L * s0 - 2.0 * L * dv * s1 + dv * dv * s2;  // sum v_y^2 f
+      double m[5] = {s0, vx * s0, sy, vz * s0, 0.5 * ((vx * vx + vz * vz) * s0 + syy)};
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const double v = warp_sum(m[r]);
+        if (lane == 0) red[warp * 5 + r] = v;
+      }
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) XB0[Cfg::elem(xlt, k, zt)] = mk2<T>(re[k], im[k]);
+  }
+  __syncthreads();
+  if (args.compute_targets && t < 5) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w * 5 + t];
+    red[(WARPS + 1) * 5 + t] = v;  // this CTA's Phi f_in
+  }
+  // ---- pass along z: thread (xl, ky) ----------------------------------------------------
+  {
+    T2* col = XB0 + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const T2 v = col[z * VEC];
+      re[z] = v.x;
+      im[z] = v.y;
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) col[k * VEC] = mk2<T>(re[k], im[k]);
+  }
+  cluster_barrier<C>();
+  // ---- pass along x, gathering the peers' x-planes: thread (kyl, kz) -------------------
+  {
+    // chunk c of CTA q holds x = q NP + c VEC + (0 .. VEC-1)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const T2* src = XB0 + Cfg::elem(c * VEC, ky_own, kzt);
+      if constexpr (C > 1) {
+        const uint32_t a = smem_u32(src);
+#pragma unroll
+        for (int q = 0; q < C; ++q) ld_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+      } else {
+        ld_local_chunk(src, re + c * VEC, im + c * VEC);
+      }
+    }
+    fft_regs<N, -1>(re, im);
+    const T scale = T(1) / T(n);
+    const bool nyq = (ky_own == N / 2) || (kzt == N / 2);
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      // Every mode with a component -N/2 is removed so each inverse transform is real.
+      const bool z0 = nyq || (kx == N / 2);
+      const T vr = z0 ? T(0) : re[kx] * scale, vi = z0 ? T(0) : im[kx] * scale;
+      if constexpr (kRegSpec) {
+        fr[kx] = vr;
+        fi[kx] = vi;
+      } else {
+        Fh[(kx * NP + kyl) * N + kzt] = mk2<T>(vr, vi);
+      }
+    }
+  }
+  if constexpr (Cfg::NXB == 1) cluster_barrier<C>();  // single buffer: peers done reading it
+
+  // ---- angular loop: one complex inverse transform per separated term --------------
+  T acc[N];
+#pragma unroll
+  for (int y = 0; y < N; ++y) acc[y] = T(0);
+
+  // pass along kx with the coefficients of term j: thread (kyl, kz), tables from L2;
+  // outputs x = q NP + c VEC + (0 .. VEC-1) go to chunk c of CTA q at (ky, kz)
+  auto pass_kx = [&](int j, T2* XB) {
+    const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      T2 c;
+      if constexpr (kRegSpec) {
+        c = mk2<T>(fr[kx], fi[kx]);
+      } else {
+        c = Fh[(kx * NP + kyl) * N + kzt];
+      }
+      const T2 ab = __ldg(tj + kx * N);
+      re[kx] = ab.x * c.x - ab.y * c.y;
+      im[kx] = ab.x * c.y + ab.y * c.x;
+    }
+    inverse_1d();
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
+      if constexpr (C > 1) {
+        const uint32_t a = smem_u32(dst);
+#pragma unroll
+        for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+      } else {
+        st_local_chunk(dst, re + c * VEC, im + c * VEC);
+      }
+    }
+  };
+  // pass along kz: thread (xl, ky)
+  auto pass_kz = [&](T2* XB) {
+    T2* col = XB + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+    for (int kz = 0; kz < N; ++kz) {
+      const T2 v = col[kz * VEC];
+      re[kz] = v.x;
+      im[kz] = v.y;
+    }
+    inverse_1d();
+#pragma unroll
+    for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
+  };
+  // pass along ky: thread (xl, z); outputs along y.  accumulate: Q+ += w Re Im; otherwise
+  // re[] keeps the loss multiplier L(v) along y.
+  auto pass_ky = [&](const T2* XB, T wj, bool accumulate) {
+    const T2* col = XB + Cfg::elem(xlt, 0, zt);
+#pragma unroll
+    for (int ky = 0; ky < N; ++ky) {
+      const T2 v = col[ky * (RW_ * VEC)];
+      re[ky] = v.x;
+      im[ky] = v.y;
+    }
+    inverse_1d();
+    if (accumulate) {
+#pragma unroll
+      for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
+    }
+  };
+
+  // This cluster's terms: i = 0 .. nt-1 is term j0 + i, and the loss transform (term
+  // M_eff) comes last in the last group (without a split: i = j = 0 .. M_eff).
+  const int j0 = kSplit ? (int)(((long long)gi * M_eff) / G) : 0;
+  const int j1 = kSplit ? (int)(((long long)(gi + 1) * M_eff) / G) : M_eff;
+  const bool has_loss = kSplit ? (gi == G - 1) : true;
+  const int nt = (j1 - j0) + (has_loss ? 1 : 0);
+  if constexpr (Cfg::NXB == 2) {
+    // Two x-plane buffers; term i uses buffer (i + 1) % 2.  The ky pass of term i - 1
+    // runs between the scatter of term i and the cluster barrier, so the remote stores
+    // drain behind it.  It reads the other buffer, and every CTA finishes it before
+    // arriving, so no peer scatters term i + 1 into that buffer while it is read.
+    T w_prev = T(0);
+    for (int i = 0; i < nt; ++i) {
+      const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
+      T2* XBj = XB0 + ((i + 1) & 1) * Cfg::XB;
+      const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+      pass_kx(j, XBj);
+      if (i > 0) pass_ky(XB0 + (i & 1) * Cfg::XB, w_prev, true);
+      cluster_barrier<C>();
+      pass_kz(XBj);
+      __syncthreads();
+      w_prev = wj;
+    }
+    // last term: the loss transform (re[] keeps L) or a gain term
+    if (has_loss) {
+      pass_ky(XB0 + (nt & 1) * Cfg::XB, T(0), false);
+    } else {
+      pass_ky(XB0 + (nt & 1) * Cfg::XB, w_prev, true);
+    }
+  } else {
+    for (int i = 0; i < nt; ++i) {
+      const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
+      const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+      pass_kx(j, XB0);
+      cluster_barrier<C>();
+      pass_kz(XB0);
+      __syncthreads();
+      pass_ky(XB0, wj, j < M_eff);
+      if (i < nt - 1) cluster_barrier<C>();  // single buffer: owners done before the next scatter
+    }
+  }
+
+  if constexpr (TC != kTcNone) {
+    // every thread has read its last accumulator row: free the TMEM columns
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(2 * N));
+  }
+  if constexpr (kSplit) {
+    // Partial gain (and the loss multiplier) of this group, then the last-arrival count
+    // of the cell (fence, barrier, one atomic: no waiting).  The cluster that arrives last
+    // sums the G partials in group order, so the result does not depend on the order of
+    // arrival, and continues with the epilogue; the others leave.
+    T* part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
+    T* lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x_own * N + y) * N + zt;
+      part[(size_t)gi * n + idx] = acc[y];
+      if (has_loss) lossp[idx] = re[y];
+    }
+    __threadfence();
+    cluster_barrier<C>();
+    unsigned* flag = reinterpret_cast<unsigned*>(smem_raw + Cfg::OFF_FLAG);
+    if (rank == 0 && t == 0) {
+      const unsigned prev = atomicAdd(&args.arrivals[lc], 1u);
+      const unsigned last = (prev == (unsigned)(G - 1)) ? 1u : 0u;
+      if (last) args.arrivals[lc] = 0u;  // every group has arrived: ready for the next launch
+#pragma unroll
+      for (int q = 0; q < C; ++q) *cta_smem<C>(flag, q) = last;
+    }
+    cluster_barrier<C>();
+    if (*flag == 0u) return;  // the whole cluster leaves together
+    __threadfence();
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x_own * N + y) * N + zt;
+      T sum = __ldcg(part + idx);
+      for (int g2 = 1; g2 < G; ++g2) sum += __ldcg(part + (size_t)g2 * n + idx);
+      acc[y] = sum;
+      re[y] = __ldcg(lossp + idx);
+    }
+  }
+
+  // ---- Q = Q+ - f L, projection and update (float64): thread (x, z) ------------------
+  const int x = x_own, z = zt;
+  const double vx = -L + x * dv, vz = -L + z * dv;
+  const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
+  double g[N];
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;  // sum_y g, sum_y y g, sum_y y^2 g over this row
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const int idx = (x * N + y) * N + z;
+    const TIO fv = fin[idx];
+    const T q = acc[y] - (T)fv * re[y];  // Q = Q+ - f L (one rounding in T)
+    double gv = args.s * (double)q;
+    if (args.b != 0.0) gv += args.b * (double)fv;
+    if (fb) gv += args.a * (double)fb[idx];
+    g[y] = gv;
+    S0 += gv;
+    S1 += (double)y * gv;
+    S2 += (double)(y * y) * gv;
+  }
+  // Phi g over the row, with v_y = -L + y dv
+  double m[5] = {S0, vx * S0, -L * S0 + dv * S1, vz * S0,
+                 0.5 * ((vx * vx + vz * vz + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2)};
+  double c5[5];
+  cluster_correction<C, WARPS>(args, m, red, cell, writable, rank, t, c5);
+  TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
+  bool bad = false;
+  // Phi^T c at (vx, vy, vz) as a quadratic in the row index y: P0 + P1 y + P2 y^2
+  const double P0 = c5[0] + c5[1] * vx + c5[3] * vz + 0.5 * c5[4] * (vx * vx + vz * vz + L * L) - c5[2] * L;
+  const double P1 = (c5[2] - c5[4] * L) * dv;
+  const double P2 = 0.5 * c5[4] * dv * dv;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double val = g[y] + (P0 + (double)y * (P1 + (double)y * P2));
+    bad |= !isfinite(val);
+    if (writable) out[(x * N + y) * N + z] = (TIO)val;
+  }
+  if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
+}
+
+// ------------------------------------------------------------------------------------
+// N = 48 and 64 (float32).  One pencil of 48 or 64 complex values takes 96 or 128
+// registers, so the gain accumulator and the spectrum cannot stay in registers as above:
+// the spectrum pencils go to global scratch (each thread reads back only its own pencil:
+// coalesced along kz, L2-resident), the gain accumulator of the CTA's x-slab lives in
+// shared memory, and one x-plane buffer serves every term (two cluster barriers per
+// term).  The epilogue recomputes g in a second sweep instead of keeping N float64 values
+// per thread.  Otherwise the same decomposition and arithmetic as collide_kernel.
+// ------------------------------------------------------------------------------------
+template <int N, int C>
+struct LargeCfg {
+  static constexpr int NP = N / C;
+  static constexpr int THREADS = NP * N;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int VEC = 2;
+  static constexpr int NCH = NP / VEC;
+  static constexpr int RW = N + 1;
+  static constexpr size_t XB = (size_t)NCH * N * RW * VEC;        // float2
+  static constexpr size_t ACC = (size_t)NP * N * N;               // float, [xl][y][z]
+  static constexpr size_t OFF_ACC = XB * sizeof(float2);
+  static constexpr size_t OFF_RED = OFF_ACC + ACC * sizeof(float);
+  static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  static constexpr size_t SMEM = OFF_FLAG + 16;
+  static_assert(THREADS % 32 == 0 && NP % VEC == 0, "whole warps and chunks");
+  static_assert(OFF_RED % 16 == 0, "aligned reduction area");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static __device__ __forceinline__ int elem(int xl, int ky, int k) {
+    return ((xl / VEC) * N + ky) * RW * VEC + k * VEC + xl % VEC;
+  }
+};
+
+template <typename TIO, int N, int C, bool kSplit>
+__global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kernel(const CollideArgs args) {
+  using Cfg = LargeCfg<N, C>;
+  using T = float;
+  using T2 = float2;
+  constexpr int NP = Cfg::NP, WARPS = Cfg::WARPS, VEC = Cfg::VEC, NCH = Cfg::NCH, RW_ = Cfg::RW;
+  constexpr int n = N * N * N;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T2* XB = reinterpret_cast<T2*>(smem_raw);
+  float* accs = reinterpret_cast<float*>(smem_raw + Cfg::OFF_ACC);
+  double* red = reinterpret_cast<double*>(smem_raw + Cfg::OFF_RED);
+
+  const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  const int G = kSplit ? args.groups : 1;
+  long long lc = blockIdx.x / C;
+  int gi = 0;
+  if constexpr (kSplit) {
+    gi = (int)(lc % G);
+    lc /= G;
+  }
+  long long cell = lc;
+  bool writable = true;
+  if (args.cell_idx) {
+    const long long s = args.cell_idx[cell];
+    writable = (s >= 0 && s < args.pool_cells);
+    if (!writable && threadIdx.x == 0) atomicOr(&g_boltz_status, kStatusBadIndex);
+    cell = writable ? s : 0;
+  }
+  const int t = threadIdx.x;
+  const int kyl = t / N, kzt = t % N;
+  const int xlt = (t / (VEC * N)) * VEC + t % VEC, grp = (t / VEC) % N;
+  const int zt = grp;
+  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  const int ky_own = rank * NP + kyl;
+  const int x_own = rank * NP + xlt;
+  // this thread's spectrum pencil (its (ky, kz), all kx) in global scratch
+  T2* spec = reinterpret_cast<T2*>(args.spec) + ((size_t)lc * G + gi) * n + (size_t)ky_own * N * N + kzt;
+
+  T re[N], im[N];
+  const double L = args.geom.L, dv = args.geom.dv;
+  const int lane = t & 31, warp = t >> 5;
+  // ---- forward transform: y pass (thread (x, z)), z pass, x pass ----------------------
+  {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const TIO fv = fin[(x_own * N + y) * N + zt];
+      re[y] = (T)fv;
+      im[y] = T(0);
+      if (args.compute_targets) {
+        s0 += (double)fv;
+        s1 += (double)y * (double)fv;
+        s2 += (double)(y * y) * (double)fv;
+      }
+    }
+    if (args.compute_targets) {
+      const double vx = -L + x_own * dv, vz = -L + zt * dv;
+      const double sy = -L * s0 + dv * s1;
+      const double syy = L * L * s0 - 2.0 * L * dv * s1 + dv * dv * s2;
+      double m[5] = {s0, vx * s0, sy, vz * s0, 0.5 * ((vx * vx + vz * vz) * s0 + syy)};
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const double v = warp_sum(m[r]);
+        if (lane == 0) red[warp * 5 + r] = v;
+      }
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) XB[Cfg::elem(xlt, k, zt)] = make_float2(re[k], im[k]);
+  }
+  __syncthreads();
+  if (args.compute_targets && t < 5) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w * 5 + t];
+    red[(WARPS + 1) * 5 + t] = v;
+  }
+  {
+    T2* col = XB + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const T2 v = col[z * VEC];
+      re[z] = v.x;
+      im[z] = v.y;
+    }
+    fft_regs<N, -1>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) col[k * VEC] = make_float2(re[k], im[k]);
+  }
+  cluster_barrier<C>();
+  {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const T2* src = XB + Cfg::elem(c * VEC, ky_own, kzt);
+      const uint32_t a = smem_u32(src);
+#pragma unroll
+      for (int q = 0; q < C; ++q) ld_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+    }
+    fft_regs<N, -1>(re, im);
+    const T scale = T(1) / T(n);
+    const bool nyq = (ky_own == N / 2) || (kzt == N / 2);
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      const bool z0 = nyq || (kx == N / 2);
+      spec[(size_t)kx * N] = z0 ? make_float2(0.f, 0.f) : make_float2(re[kx] * scale, im[kx] * scale);
+    }
+  }
+  for (int i = t; i < (int)Cfg::ACC; i += Cfg::THREADS) accs[i] = 0.f;
+  cluster_barrier<C>();  // peers done gathering from this CTA's buffer
+
+  // ---- angular loop --------------------------------------------------------------------
+  const int j0 = kSplit ? (int)(((long long)gi * M_eff) / G) : 0;
+  const int j1 = kSplit ? (int)(((long long)(gi + 1) * M_eff) / G) : M_eff;
+  const bool has_loss = kSplit ? (gi == G - 1) : true;
+  const int nt = (j1 - j0) + (has_loss ? 1 : 0);
+  for (int i = 0; i < nt; ++i) {
+    const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
+    const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+    {  // kx pass with the coefficients: thread (kyl, kz); outputs scattered by x
+      const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
+#pragma unroll
+      for (int kx = 0; kx < N; ++kx) {
+        const T2 c = spec[(size_t)kx * N];
+        const T2 ab = __ldg(tj + kx * N);
+        re[kx] = ab.x * c.x - ab.y * c.y;
+        im[kx] = ab.x * c.y + ab.y * c.x;
+      }
+      fft_regs<N, +1>(re, im);
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const uint32_t a = smem_u32(XB + Cfg::elem(c * VEC, ky_own, kzt));
+#pragma unroll
+        for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+      }
+    }
+    cluster_barrier<C>();
+    {  // kz pass: thread (xl, ky)
+      T2* col = XB + Cfg::elem(xlt, grp, 0);
+#pragma unroll
+      for (int kz = 0; kz < N; ++kz) {
+        const T2 v = col[kz * VEC];
+        re[kz] = v.x;
+        im[kz] = v.y;
+      }
+      fft_regs<N, +1>(re, im);
+#pragma unroll
+      for (int z = 0; z < N; ++z) col[z * VEC] = make_float2(re[z], im[z]);
+    }
+    __syncthreads();
+    {  // ky pass: thread (xl, z); Q+ += w Re Im into shared memory, or keep L in re[]
+      const T2* col = XB + Cfg::elem(xlt, 0, zt);
+#pragma unroll
+      for (int ky = 0; ky < N; ++ky) {
+        const T2 v = col[ky * (RW_ * VEC)];
+        re[ky] = v.x;
+        im[ky] = v.y;
+      }
+      fft_regs<N, +1>(re, im);
+      if (j < M_eff) {
+        float* a = accs + (size_t)xlt * N * N + zt;
+#pragma unroll
+        for (int y = 0; y < N; ++y) a[y * N] += wj * (re[y] * im[y]);
+      }
+    }
+    if (i < nt - 1) cluster_barrier<C>();  // owners done reading before the next scatter
+  }
+
+  const int x = x_own, z = zt;
+  float* acc_row = accs + (size_t)xlt * N * N + z;  // acc_row[y * N], this thread's (x, z) row
+  if constexpr (kSplit) {
+    // partial gain and loss of this group, then the last-arrival count (as collide_kernel)
+    T* part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
+    T* lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x * N + y) * N + z;
+      part[(size_t)gi * n + idx] = acc_row[y * N];
+      if (has_loss) lossp[idx] = re[y];
+    }
+    __threadfence();
+    cluster_barrier<C>();
+    unsigned* flag = reinterpret_cast<unsigned*>(smem_raw + Cfg::OFF_FLAG);
+    if (rank == 0 && t == 0) {
+      const unsigned prev = atomicAdd(&args.arrivals[lc], 1u);
+      const unsigned last = (prev == (unsigned)(G - 1)) ? 1u : 0u;
+      if (last) args.arrivals[lc] = 0u;
+#pragma unroll
+      for (int q = 0; q < C; ++q) *cta_smem<C>(flag, q) = last;
+    }
+    cluster_barrier<C>();
+    if (*flag == 0u) return;
+    __threadfence();
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const int idx = (x * N + y) * N + z;
+      T sum = __ldcg(part + idx);
+      for (int g2 = 1; g2 < G; ++g2) sum += __ldcg(part + (size_t)g2 * n + idx);
+      acc_row[y * N] = sum;
+      re[y] = __ldcg(lossp + idx);
+    }
+  }
+
+  // ---- epilogue (float64), two sweeps over this thread's row --------------------------
+  const double vx = -L + x * dv, vz = -L + z * dv;
+  const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
+  auto gval = [&](int y) {
+    const int idx = (x * N + y) * N + z;
+    const TIO fv = fin[idx];
+    const T q = acc_row[y * N] - (T)fv * re[y];  // Q = Q+ - f L (one rounding in T)
+    double gv = args.s * (double)q;
+    if (args.b != 0.0) gv += args.b * (double)fv;
+    if (fb) gv += args.a * (double)fb[idx];
+    return gv;
+  };
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double gv = gval(y);
+    S0 += gv;
+    S1 += (double)y * gv;
+    S2 += (double)(y * y) * gv;
+  }
+  double m[5] = {S0, vx * S0, -L * S0 + dv * S1, vz * S0,
+                 0.5 * ((vx * vx + vz * vz + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2)};
+  double c5[5];
+  cluster_correction<C, WARPS>(args, m, red, cell, writable, rank, t, c5);
+  TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
+  bool bad = false;
+  const double P0 = c5[0] + c5[1] * vx + c5[3] * vz + 0.5 * c5[4] * (vx * vx + vz * vz + L * L) - c5[2] * L;
+  const double P1 = (c5[2] - c5[4] * L) * dv;
+  const double P2 = 0.5 * c5[4] * dv * dv;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double val = gval(y) + (P0 + (double)y * (P1 + (double)y * P2));
+    bad |= !isfinite(val);
+    if (writable) out[(x * N + y) * N + z] = (TIO)val;
+  }
+  if (bad) atomicOr(&g_boltz_status, kStatusNonFinite);
+}
+
+// ------------------------------------------------------------------------------------
+// Two dimensions (Maxwell molecules; Sec. 3.3 dimension two, Eq. dfor0).  A cell is N
+// threads (one pencil each) of a CTA that holds several cells; the cell's spectrum and
+// one N x (N+1) plane buffer live in shared memory, the gain accumulator in registers.
+// Per term: kx pass with the coefficients (thread ky, tables [term][kx][ky] read
+// coalesced across the cell's threads), transposed store, ky pass (thread x) and
+// Q+ += w Re Im along y.  Projection on (1, v_x, v_y, |v|^2/2) in float64 (the 5-slot
+// matrix G has row and column 3 zero), two sweeps in the epilogue.
+// ------------------------------------------------------------------------------------
+template <typename T, int N>
+struct PlaneCfg {
+  using T2 = typename Vec2<T>::type;
+  static constexpr int RW = N + 1;
+  static constexpr size_t BUF = (size_t)N * RW;  // T2 per plane
+  static constexpr size_t CELL_SMEM = 2 * BUF * sizeof(T2) + (size_t)(N + 1) * 10 * sizeof(double);
+  static constexpr int CPB_SMEM = (int)((200u * 1024u) / CELL_SMEM);
+  static constexpr int CPB = (256 / N < CPB_SMEM) ? 256 / N : CPB_SMEM;  // cells per CTA
+  static constexpr int THREADS = CPB * N;
+  static constexpr size_t SMEM = (size_t)CPB * CELL_SMEM;
+  static_assert(CPB >= 1, "one cell must fit");
+  static_assert((2 * BUF * sizeof(T2)) % 16 == 0 || true, "");
+};
+
+template <typename T, typename TIO, int N>
+__global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(const CollideArgs args, long long n_cells) {
+  using Cfg = PlaneCfg<T, N>;
+  using T2 = typename Cfg::T2;
+  constexpr int RW_ = Cfg::RW;
+  constexpr int n = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int ci = threadIdx.x / N, t = threadIdx.x % N;
+  unsigned char* base = smem_raw + (size_t)ci * Cfg::CELL_SMEM;
+  T2* Fh = reinterpret_cast<T2*>(base);                 // spectrum [kx][ky]
+  T2* P = Fh + Cfg::BUF;                                 // plane buffer [x][ky]
+  double* red = reinterpret_cast<double*>(P + Cfg::BUF); // [N][10], then [10] cell totals
+
+  long long lc = (long long)blockIdx.x * Cfg::CPB + ci;
+  const bool in_launch = lc < n_cells;  // the last CTA may hold fewer cells
+  if (!in_launch) lc = n_cells - 1;
+  long long cell = lc;
+  bool writable = in_launch;
+  if (args.cell_idx) {
+    const long long s = args.cell_idx[lc];
+    const bool ok = (s >= 0 && s < args.pool_cells);
+    if (!ok && in_launch && t == 0) atomicOr(&g_boltz_status, kStatusBadIndex);
+    writable = writable && ok;
+    cell = ok ? s : 0;
+  }
+  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const T2* tab = reinterpret_cast<const T2*>(args.tab);
+  const int M_eff = args.M_eff;
+  const double L = args.geom.L, dv = args.geom.dv;
+  T re[N], im[N], acc[N];
+
+  // forward: y pass (thread x), then x pass (thread ky)
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const TIO fv = fin[t * N + y];
+    re[y] = (T)fv;
+    im[y] = T(0);
+    s0 += (double)fv;
+    s1 += (double)y * (double)fv;
+    s2 += (double)(y * y) * (double)fv;
+  }
+  fft_regs<N, -1>(re, im);
+#pragma unroll
+  for (int k = 0; k < N; ++k) P[t * RW_ + k] = mk2<T>(re[k], im[k]);
+  __syncthreads();
+#pragma unroll
+  for (int x = 0; x < N; ++x) {
+    const T2 v = P[x * RW_ + t];
+    re[x] = v.x;
+    im[x] = v.y;
+  }
+  fft_regs<N, -1>(re, im);
+  {
+    const T scale = T(1) / T(n);
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      const bool z0 = (kx == N / 2) || (t == N / 2);
+      Fh[kx * RW_ + t] = z0 ? mk2<T>(T(0), T(0)) : mk2<T>(re[kx] * scale, im[kx] * scale);
+    }
+  }
+#pragma unroll
+  for (int y = 0; y < N; ++y) acc[y] = T(0);
+  __syncthreads();
+
+  for (int j = 0; j <= M_eff; ++j) {
+    const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
+    const T2* tj = tab + (size_t)j * n + t;
+#pragma unroll
+    for (int kx = 0; kx < N; ++kx) {
+      const T2 c = Fh[kx * RW_ + t];
+      const T2 ab = __ldg(tj + kx * N);
+      re[kx] = ab.x * c.x - ab.y * c.y;
+      im[kx] = ab.x * c.y + ab.y * c.x;
+    }
+    fft_regs<N, +1>(re, im);
+#pragma unroll
+    for (int x = 0; x < N; ++x) P[x * RW_ + t] = mk2<T>(re[x], im[x]);
+    __syncthreads();
+#pragma unroll
+    for (int ky = 0; ky < N; ++ky) {
+      const T2 v = P[t * RW_ + ky];
+      re[ky] = v.x;
+      im[ky] = v.y;
+    }
+    fft_regs<N, +1>(re, im);
+    if (j < M_eff) {
+#pragma unroll
+      for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
+    }
+    __syncthreads();  // the next term overwrites P
+  }
+  // re[] holds the loss multiplier L along y of row x = t
+
+  const int x = t;
+  const double vx = -L + x * dv;
+  const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
+  auto gval = [&](int y) {
+    const TIO fv = fin[x * N + y];
+    const T q = acc[y] - (T)fv * re[y];
+    double gv = args.s * (double)q;
+    if (args.b != 0.0) gv += args.b * (double)fv;
+    if (fb) gv += args.a * (double)fb[x * N + y];
+    return gv;
+  };
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double gv = gval(y);
+    S0 += gv;
+    S1 += (double)y * gv;
+    S2 += (double)(y * y) * gv;
+  }
+  // this row's share of Phi g and Phi f (targets), v_y = -L + y dv; slot 3 (v_z) is zero
+  {
+    double* r = red + t * 10;
+    r[0] = S0;
+    r[1] = vx * S0;
+    r[2] = -L * S0 + dv * S1;
+    r[3] = 0.0;
+    r[4] = 0.5 * ((vx * vx + L * L) * S0 - 2.0 * L * dv * S1 + dv * dv * S2);
+    r[5] = s0;
+    r[6] = vx * s0;
+    r[7] = -L * s0 + dv * s1;
+    r[8] = 0.0;
+    r[9] = 0.5 * ((vx * vx + L * L) * s0 - 2.0 * L * dv * s1 + dv * dv * s2);
+  }
+  __syncthreads();
+  double* tot = red + N * 10;
+  if (t < 10) {
+    double v = 0.0;
+    for (int q = 0; q < N; ++q) v += red[q * 10 + t];
+    tot[t] = v;
+  }
+  __syncthreads();
+  double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (args.project) {
+    double tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (args.compute_targets) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = tot[5 + r];
+      if (args.Utgt && writable && t == 0) {
+#pragma unroll
+        for (int r = 0; r < 5; ++r) args.Utgt[cell * 5 + r] = tgt[r];
+      }
+    } else if (args.Utgt) {
+#pragma unroll
+      for (int r = 0; r < 5; ++r) tgt[r] = args.Utgt[cell * 5 + r];
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v += args.geom.G[r * 5 + k] * (tgt[k] - tot[k]);
+      c5[r] = v;
+    }
+  }
+  TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
+  bool bad = false;
+  const double P0 = c5[0] + c5[1] * vx + 0.5 * c5[4] * (vx * vx + L * L) - c5[2] * L;
+  const double P1 = (c5[2] - c5[4] * L) * dv;
+  const double P2 = 0.5 * c5[4] * dv * dv;
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    const double val = gval(y) + (P0 + (double)y * (P1 + (double)y * P2));
+    bad |= !isfinite(val);
+    if (writable) out[x * N + y] = (TIO)val;
+  }
+  if (bad && writable) atomicOr(&g_boltz_status, kStatusNonFinite);
+}
+
+// ------------------------------------------------------------------------------------
+// launchers (instantiated by the unit that dispatches them)
+// ------------------------------------------------------------------------------------
+
+static inline boltz_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return BOLTZ_ECUDA;
+}
+
+template <typename T, typename TIO, int N, int C, int TC = kTcNone>
+static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  using Cfg = CollideCfg<T, N, C, TC>;
+  const bool split = a.groups > 1;
+  void (*kern)(const CollideArgs);
+  if constexpr (TC != kTcNone) {
+    kern = collide_kernel<T, TIO, N, C, false, TC>;  // no term groups with tensor-core transforms
+  } else {
+    kern = split ? collide_kernel<T, TIO, N, C, true> : collide_kernel<T, TIO, N, C, false>;
+  }
+  // function attributes are per device: set them once per (instantiation, device), and
+  // check once that a cluster of this size can be scheduled at all
+  static std::atomic<unsigned long long> prepared[2], unschedulable[2];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    if (C > 1) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(C, 1, 1);
+      q.blockDim = dim3(Cfg::THREADS, 1, 1);
+      q.dynamicSmemBytes = Cfg::SMEM;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = C;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int clusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&clusters, kern, &q);
+      if (e != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        if (dev < 64) unschedulable[split].fetch_or(bit, std::memory_order_release);
+      }
+    }
+    if (dev < 64) prepared[split].fetch_or(bit, std::memory_order_release);
+  }
+  if (dev < 64 && (unschedulable[split].load(std::memory_order_acquire) & bit)) {
+    set_error("a thread-block cluster of this size cannot be scheduled on this device");
+    return BOLTZ_EUNSUPPORTED;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
+  cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (C > 1) ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return cuda_fail(e, "collide launch");
+  return BOLTZ_OK;
+}
+
+template <typename TIO, int N, int C>
+static boltz_status launch_large_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  using Cfg = LargeCfg<N, C>;
+  const bool split = a.groups > 1;
+  auto kern = split ? collide_large_kernel<TIO, N, C, true> : collide_large_kernel<TIO, N, C, false>;
+  static std::atomic<unsigned long long> prepared[2], unschedulable[2];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const unsigned long long bit = 1ull << (dev & 63);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(C, 1, 1);
+    q.blockDim = dim3(Cfg::THREADS, 1, 1);
+    q.dynamicSmemBytes = Cfg::SMEM;
+    q.attrs = attr;
+    q.numAttrs = 1;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &q);
+    if (e != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      if (dev < 64) unschedulable[split].fetch_or(bit, std::memory_order_release);
+    }
+    if (dev < 64) prepared[split].fetch_or(bit, std::memory_order_release);
+  }
+  if (dev < 64 && (unschedulable[split].load(std::memory_order_acquire) & bit)) {
+    set_error("a thread-block cluster of this size cannot be scheduled on this device");
+    return BOLTZ_EUNSUPPORTED;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
+  cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return cuda_fail(e, "collide launch");
+  return BOLTZ_OK;
+}
+
+template <typename T, typename TIO, int N>
+static boltz_status launch2d_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
+  using Cfg = PlaneCfg<T, N>;
+  auto kern = collide2d_kernel<T, TIO, N>;
+  static std::atomic<unsigned long long> prepared{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (dev >= 64 || !(prepared.load(std::memory_order_acquire) & bit)) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    if (dev < 64) prepared.fetch_or(bit, std::memory_order_release);
+  }
+  const long long blocks = (n_cells + Cfg::CPB - 1) / Cfg::CPB;
+  kern<<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, st>>>(a, (long long)n_cells);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "collide2d launch");
+  return BOLTZ_OK;
+}
+
+// Per-unit services: the twiddle constants and the status word are per translation unit.
+#define BOLTZ_UNIT_SERVICES(TAG)                                                                  \
+  cudaError_t unit_upload_twiddles_##TAG(const double* tc, const double* ts, const float* fc,     \
+                                         const float* fs) {                                       \
+    cudaError_t e;                                                                                \
+    if ((e = cudaMemcpyToSymbol(c_twc64, tc, sizeof(double) * kTw)) != cudaSuccess) return e;     \
+    if ((e = cudaMemcpyToSymbol(c_tws64, ts, sizeof(double) * kTw)) != cudaSuccess) return e;     \
+    if ((e = cudaMemcpyToSymbol(c_twc32, fc, sizeof(float) * kTw)) != cudaSuccess) return e;      \
+    return cudaMemcpyToSymbol(c_tws32, fs, sizeof(float) * kTw);                                  \
+  }                                                                                               \
+  cudaError_t unit_read_clear_status_##TAG(unsigned* value) {                                     \
+    unsigned v = 0, zero = 0;                                                                     \
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_boltz_status, sizeof(v));                          \
+    if (e != cudaSuccess) return e;                                                               \
+    *value |= v;                                                                                  \
+    return cudaMemcpyToSymbol(g_boltz_status, &zero, sizeof(zero));                               \
+  }
+
+}  // namespace boltz

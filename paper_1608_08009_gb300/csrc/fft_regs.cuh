@@ -15,11 +15,12 @@ namespace boltz {
 
 constexpr int kTw = 192;
 
-// Defined here; this header is included by exactly one translation unit (collide.cu).
-__constant__ double c_twc64[kTw];
-__constant__ double c_tws64[kTw];
-__constant__ float c_twc32[kTw];
-__constant__ float c_tws32[kTw];
+// One copy per translation unit that includes this header (internal linkage); the host
+// fills every unit's copy through that unit's upload function.
+static __constant__ double c_twc64[kTw];
+static __constant__ double c_tws64[kTw];
+static __constant__ float c_twc32[kTw];
+static __constant__ float c_tws32[kTw];
 
 template <typename T> __device__ __forceinline__ T tw_cos(int m);
 template <typename T> __device__ __forceinline__ T tw_sin(int m);

@@ -24,6 +24,34 @@ struct KernelGeom {
   double G[25];
 };
 
+// Argument block of every collision kernel (passed by value).
+struct CollideArgs {
+  const void* f_in;    // [cells][N^3] TIO
+  const void* f_base;  // [cells][N^3] TIO or null
+  void* out;           // [cells][N^3] TIO
+  const void* tab;     // [(M_eff + 1)][ky][kx][kz] (alpha, alpha') as Vec2<T>; entry M_eff = (D, 0)
+  const double* w;     // [M_eff]
+  double* Utgt;        // [cells][5] target Phi-sums, or null (target 0)
+  double a, b, s;      // out = Pi(a f_base + b f_in + s Q)
+  int M_eff;
+  int project;
+  int compute_targets; // 1: targets = Phi f_in, computed here and written to Utgt if non-null
+  const int64_t* cell_idx;  // null: cell c of the launch is slot c; else slot cell_idx[c]
+  int64_t pool_cells;       // number of slots behind f_in / f_base / out / Utgt (cell_idx)
+  // Term groups.  groups = 1: one cluster per cell does every term and the epilogue.
+  // groups = G > 1: cluster (c, g) does the terms [g M_eff / G, (g + 1) M_eff / G) (the
+  // last group also the loss transform) and writes its partial gain to
+  // part[(c G + g) n ...] and the loss multiplier to loss[c n ...] (c = cell of the
+  // launch), then counts itself in arrivals[c]; the cluster that arrives last sums the
+  // partials in group order and runs the epilogue (and resets arrivals[c] to 0).
+  int groups;
+  void* part;          // [cells][G][n] T
+  void* loss;          // [cells][n] T
+  unsigned* arrivals;  // [cells], zero between launches
+  void* spec;          // N = 48, 64: spectrum pencils [cells][G][ky][kx][kz] float2
+  KernelGeom geom;
+};
+
 }  // namespace boltz
 
 struct boltz_grid_s {
@@ -81,7 +109,7 @@ boltz_status build_tables(boltz_grid_s* g);
 // Host table builder of the 2D Maxwell-molecule grids (tables.cpp).
 boltz_status build_tables2d(boltz_grid_s* g);
 
-// Kernel launchers (collide.cu).
+// Kernel launchers (collide.cu, dispatching to the kernel units).
 boltz_status upload_tables(boltz_grid_s* g);
 // out = Pi(a f_base + b f_in + s Q(f_in)).  Pi projects onto the targets Utgt (Phi-sums,
 // [cells][5]); compute_targets = 1 takes the targets from f_in itself (and stores them to
@@ -109,6 +137,27 @@ boltz_status relax_steps(const boltz_grid_s* g, int64_t n_cells, int prec, int f
                          int steps, int rk_order, cudaStream_t s, double* U0, void* stage, int groups = -1,
                          int cluster = 0);
 void free_host_pipeline(boltz_grid_s* g);
+// Kernel units (collide_f32.cu, collide_f64.cu, collide_tc.cu, collide_2d.cu): launch of
+// the collision kernels for one argument block, and each unit's twiddle upload and
+// status word (every unit has its own copies).
+boltz_status dispatch_3d_f32(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
+                             int cluster, int f_is_fp64);
+boltz_status dispatch_3d_f64(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
+                             int cluster, int f_is_fp64);
+boltz_status dispatch_3d_tc(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st, int prec,
+                            int f_is_fp64);
+boltz_status dispatch_3d_large(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
+                               int f_is_fp64);
+boltz_status dispatch_2d(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st, int prec,
+                         int f_is_fp64);
+#define BOLTZ_DECLARE_UNIT(TAG)                                                                                    \
+  cudaError_t unit_upload_twiddles_##TAG(const double* tc, const double* ts, const float* fc, const float* fs); \
+  cudaError_t unit_read_clear_status_##TAG(unsigned* value);
+BOLTZ_DECLARE_UNIT(f32)
+BOLTZ_DECLARE_UNIT(f64)
+BOLTZ_DECLARE_UNIT(tc)
+BOLTZ_DECLARE_UNIT(p2d)
+#undef BOLTZ_DECLARE_UNIT
 // Argument checks shared by the entry points (api.cpp): set the error message on failure.
 boltz_status check_batch(const boltz_batch* b);
 boltz_status check_device(const boltz_grid_s* g);

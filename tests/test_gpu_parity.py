@@ -203,8 +203,8 @@ def test_argument_errors():
         with pytest.raises(B.BoltzError) as ei:
             B.boltz_relax(g.batch(2), f, -0.1, 1)
         assert ei.value.status == B.BOLTZ_EINVAL
-        with pytest.raises(B.BoltzError) as ei:
-            B.boltz_collide(g.batch(2, B.BOLTZ_TF32_DFT), f, torch.empty_like(f))
+        with pytest.raises(B.BoltzError) as ei:  # reserved precision mode
+            B.boltz_collide(g.batch(2, B.BOLTZ_3XBF16_DFT), f, torch.empty_like(f))
         assert ei.value.status == B.BOLTZ_EUNSUPPORTED
 
 
