@@ -61,7 +61,9 @@ typedef enum {
                               contraction on the tensor cores (tcgen05, kind::tf32, f32
                               accumulate in TMEM); inputs rounded to tf32 (~1e-3 relative
                               per pass).  N = 16, 32; reduced-precision comparison mode  */
-  BOLTZ_3XBF16_DFT = 3,    /* reserved (returns BOLTZ_EUNSUPPORTED)                     */
+  BOLTZ_3XBF16_DFT = 3,    /* as BOLTZ_TF32_DFT on kind::f16 with bf16 operands split into
+                              high and low parts (Ah Wh + Ah Wl + Al Wh): ~16 significant
+                              bits per product, ~1e-4 relative per pass                 */
   BOLTZ_3XTF32_DFT = 4     /* as BOLTZ_TF32_DFT with operands split into tf32 high and
                               low parts, Ah Wh + Ah Wl + Al Wh: float32-class accuracy  */
 } boltz_precision;

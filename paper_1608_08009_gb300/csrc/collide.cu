@@ -209,7 +209,7 @@ bool collide_supported_grid(const boltz_grid_s* g, int prec) {
 }
 
 bool collide_supported(int N, int prec) {
-  if (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XTF32_DFT) return N == 16 || N == 32;
+  if (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XBF16_DFT || prec == BOLTZ_3XTF32_DFT) return N == 16 || N == 32;
   if (N == 8 || N == 16 || N == 24 || N == 32) return prec == BOLTZ_FP64 || prec == BOLTZ_FP32_FFT;
   if (N == 48 || N == 64) return prec == BOLTZ_FP32_FFT;  // float64 pencils of 48/64 do not fit
   return false;
@@ -310,7 +310,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
     return dispatch_2d(g, a2, n_cells, stream, prec, f_is_fp64);
   }
   if (cluster == 0 && prec != BOLTZ_FP64) cluster = g->cluster_size;  // 0: the default of (N, prec)
-  const bool tc = (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XTF32_DFT);
+  const bool tc = (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XBF16_DFT || prec == BOLTZ_3XTF32_DFT);
   int G = tc ? 1 : (groups < 0 ? g->term_groups : groups);
   G = std::max(1, std::min(G, g->M_eff));
   if (n_cells * (int64_t)G * 16 > (int64_t)INT32_MAX) {
@@ -369,7 +369,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
     return dispatch_3d_f64(g, args, n_cells, stream, cluster, f_is_fp64);
   }
   args.tab = g->tab32;
-  if (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XTF32_DFT) return dispatch_3d_tc(g, args, n_cells, stream, prec, f_is_fp64);
+  if (tc) return dispatch_3d_tc(g, args, n_cells, stream, prec, f_is_fp64);
   if (g->N > 32) return dispatch_3d_large(g, args, n_cells, stream, f_is_fp64);
   return dispatch_3d_f32(g, args, n_cells, stream, cluster, f_is_fp64);
 }

@@ -61,7 +61,7 @@ constexpr unsigned kStatusBadIndex = 4u;
 constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on a tensor-core barrier gave up
 
 // Tensor-core transform modes of the float32 path (0: register FFT).
-constexpr int kTcNone = 0, kTcTF32 = 1, kTc3xTF32 = 3;
+constexpr int kTcNone = 0, kTcTF32 = 1, kTc3xBF16 = 2, kTc3xTF32 = 3;
 
 template <typename T, int N, int C, int TC = kTcNone>
 struct CollideCfg {
@@ -71,8 +71,10 @@ struct CollideCfg {
   // CTAs per SM asked of the register allocator.  float32 32^3 with C = 8: 3 (168
   // registers, 44 bytes spilled outside the term loop) runs 11 % faster on GB300 than the
   // 252-register 2-CTA version: twelve warps hide the table loads and barrier waits.
-  static constexpr int MIN_BLOCKS =
-      (TC == kTcTF32) ? 2 : (TC == kTc3xTF32) ? 1 : (sizeof(T) == 4 && N == 32 && C == 8) ? 3 : 1;
+  static constexpr int MIN_BLOCKS = (TC == kTcTF32 || TC == kTc3xBF16) ? 2
+                                    : (TC == kTc3xTF32)                  ? 1
+                                    : (sizeof(T) == 4 && N == 32 && C == 8) ? 3
+                                                                            : 1;
   using T2 = typename Vec2<T>::type;
   static constexpr bool kF32 = sizeof(T) == 4;
   // float32: the spectrum pencil of each thread stays in registers and the x-plane
@@ -100,11 +102,12 @@ struct CollideCfg {
   // 8-row x 16-byte core matrices, K-adjacent ones 128 bytes apart), the DFT matrix,
   // the MMA-completion barrier and the TMEM address
   static constexpr int TC_K = 2 * N;
-  static constexpr int TC_SPLIT = (TC == kTc3xTF32) ? 2 : 1;
+  static constexpr int TC_SPLIT = (TC == kTc3xTF32 || TC == kTc3xBF16) ? 2 : 1;
+  static constexpr int TC_ES = (TC == kTc3xBF16) ? 2 : 4;  // operand element bytes
   static constexpr size_t OFF_TCA = (OFF_FLAG + 16 + 1023) / 1024 * 1024;
-  static constexpr size_t TCA_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * THREADS * TC_K * 4 : 0;
+  static constexpr size_t TCA_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * THREADS * TC_K * TC_ES : 0;
   static constexpr size_t OFF_TCW = OFF_TCA + TCA_BYTES;
-  static constexpr size_t TCW_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * TC_K * TC_K * 4 : 0;
+  static constexpr size_t TCW_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * TC_K * TC_K * TC_ES : 0;
   static constexpr size_t OFF_TCB = OFF_TCW + TCW_BYTES;  // mbarrier (8 B) + TMEM address (4 B)
   static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 16;
   static_assert(TC == kTcNone || (kF32 && THREADS == 128), "tensor-core transforms: float32, 128 pencils per CTA");
@@ -239,24 +242,28 @@ __device__ __forceinline__ void cluster_correction(const CollideArgs& args, cons
   cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
 }
 
-// ---- tensor-core 1D DFT of 128 pencils (tcgen05, kind::tf32) --------------------------
+// ---- tensor-core 1D DFT of 128 pencils (tcgen05) ------------------------------------
 // Each thread of the CTA holds one pencil of N complex values.  The inverse DFT of all
 // 128 pencils is one dense contraction D[128 x 2N] = A[128 x 2N] W[2N x 2N] with the real
 // block form A = [re | im], W = [[C, S], [-S, C]] (C, S = cos, sin of 2 pi x k / N): rows
 // go to shared memory, one thread issues the MMAs (accumulator in TMEM), the others wait
 // on an mbarrier with a bounded number of tries, and every thread reads its row back
-// with tcgen05.ld.  3xTF32 splits A and W into tf32 high and low parts and accumulates
-// Ah Wh + Ah Wl + Al Wh (the Al Wl term is below float32 rounding).
+// with tcgen05.ld.  Modes: TF32 (kind::tf32, operands rounded to tf32); 3xTF32 and
+// 3xBF16 split both operands into high and low parts of that type and accumulate
+// Ah Wh + Ah Wl + Al Wh (kind::tf32, or kind::f16 with bf16 operands); the Al Wl term is
+// below the split's resolution.
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
 
-// float index of element (row, k) of a K-major, no-swizzle tile with K columns
-template <int K>
-__device__ __forceinline__ int kmajor(int row, int k) {
-  return (row / 8) * (K * 8) + (k / 4) * 32 + (row % 8) * 4 + (k % 4);
+// bf16 round-to-nearest-even of x, returned as its 16-bit pattern and its float value
+__device__ __forceinline__ uint16_t to_bf16(float x, float& back) {
+  uint16_t h;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  back = __uint_as_float((uint32_t)h << 16);
+  return h;
 }
 
 // shared-memory matrix descriptor: start, leading (K) and stride (8-row) byte offsets,
@@ -269,14 +276,26 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 template <int N, int TC>
 struct TcDft {
   static constexpr int K = 2 * N;
-  float* A;           // [TC_SPLIT][128 x K]
-  const float* W;     // [TC_SPLIT][K x K] as B operand rows n (output), K-major
+  static constexpr bool kBF16 = (TC == kTc3xBF16);
+  static constexpr bool kSplit = (TC == kTc3xTF32 || TC == kTc3xBF16);
+  static constexpr int ES = kBF16 ? 2 : 4;   // element bytes
+  static constexpr int EPC = 16 / ES;        // elements per 16-byte core-matrix row
+  static constexpr int SBO = (K / EPC) * 128;  // bytes between 8-row groups
+  static constexpr int KSTEP = 32 / ES;      // K per MMA instruction (32 bytes)
+  unsigned char* A;         // [split][128 x K] K-major, no swizzle
+  const unsigned char* W;   // [split][K x K] as B operand rows n (output), K-major
   uint64_t* mbar;
   uint32_t tmem;
   uint32_t phase;
 
-  // the inverse-DFT matrix from the twiddle table, high and low tf32 parts
-  __device__ static void build_w(float* Wdst, int t, int nthreads) {
+  // byte offset of element (row, k): 8-row x 16-byte core matrices, K-adjacent ones 128
+  // bytes apart, 8-row groups SBO apart
+  __device__ static __forceinline__ int offs(int row, int k) {
+    return (row / 8) * SBO + (k / EPC) * 128 + (row % 8) * 16 + (k % EPC) * ES;
+  }
+
+  // the inverse-DFT matrix from the twiddle table, high (and low) parts
+  __device__ static void build_w(unsigned char* Wdst, int t, int nthreads) {
     constexpr int stride = kTw / N;
     for (int i = t; i < K * K; i += nthreads) {
       const int nn = i / K, k = i % K;  // output index, input index
@@ -286,44 +305,76 @@ struct TcDft {
       float v;
       if (nn < N) v = (k < N) ? c : -sn;   // Re y = C Re a - S Im a
       else v = (k < N) ? sn : c;           // Im y = S Re a + C Im a
-      const float hi = to_tf32(v);
-      Wdst[kmajor<K>(nn, k)] = hi;
-      if (TC == kTc3xTF32) Wdst[K * K + kmajor<K>(nn, k)] = to_tf32(v - hi);
+      if constexpr (kBF16) {
+        float hb, lb;
+        const uint16_t h = to_bf16(v, hb);
+        const uint16_t l = to_bf16(v - hb, lb);
+        *reinterpret_cast<uint16_t*>(Wdst + offs(nn, k)) = h;
+        *reinterpret_cast<uint16_t*>(Wdst + K * K * ES + offs(nn, k)) = l;
+      } else {
+        const float hi = to_tf32(v);
+        *reinterpret_cast<float*>(Wdst + offs(nn, k)) = hi;
+        if constexpr (kSplit) *reinterpret_cast<float*>(Wdst + K * K * ES + offs(nn, k)) = to_tf32(v - hi);
+      }
     }
   }
 
   __device__ __forceinline__ void mma_set(uint32_t a_addr, uint32_t b_addr, bool first) const {
-    // D f32, A and B tf32, both K-major, N = K, M = 128
-    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K >> 3) << 17) | ((128u >> 4) << 24);
+    // D f32; A and B tf32 (2) or bf16 (1); both K-major; N = K; M = 128
+    constexpr uint32_t fmt = kBF16 ? 1u : 2u;
+    constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(K >> 3) << 17) | ((128u >> 4) << 24);
 #pragma unroll
-    for (int s = 0; s < K / 8; ++s) {
-      const uint64_t ad = umma_desc(a_addr + s * 256, 128, K * 32);
-      const uint64_t bd = umma_desc(b_addr + s * 256, 128, K * 32);
+    for (int s = 0; s < K / KSTEP; ++s) {
+      const uint64_t ad = umma_desc(a_addr + s * 256, 128, SBO);
+      const uint64_t bd = umma_desc(b_addr + s * 256, 128, SBO);
       const uint32_t acc = (first && s == 0) ? 0u : 1u;
-      asm volatile(
-          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      if constexpr (kBF16) {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      } else {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+    }
+  }
+
+  // 8 values of the row (bf16: one 16-byte chunk; tf32: two) at k0, high and low parts
+  __device__ __forceinline__ void put8(int t, int k0, const float* v) {
+    if constexpr (kBF16) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float h0, h1, l0, l1;
+        const uint16_t a0 = to_bf16(v[2 * q], h0), a1 = to_bf16(v[2 * q + 1], h1);
+        const uint16_t b0 = to_bf16(v[2 * q] - h0, l0), b1 = to_bf16(v[2 * q + 1] - h1, l1);
+        hw[q] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+        lw[q] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+      }
+      *reinterpret_cast<uint4*>(A + offs(t, k0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(A + 128 * K * ES + offs(t, k0)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; q += 4) {
+        const float4 h = make_float4(to_tf32(v[q]), to_tf32(v[q + 1]), to_tf32(v[q + 2]), to_tf32(v[q + 3]));
+        *reinterpret_cast<float4*>(A + offs(t, k0 + q)) = h;
+        if constexpr (kSplit)
+          *reinterpret_cast<float4*>(A + 128 * K * ES + offs(t, k0 + q)) =
+              make_float4(to_tf32(v[q] - h.x), to_tf32(v[q + 1] - h.y), to_tf32(v[q + 2] - h.z),
+                          to_tf32(v[q + 3] - h.w));
+      }
     }
   }
 
   // inverse DFT of this thread's pencil (re, im) in place; all 128 threads call it
   __device__ __forceinline__ void inverse(float (&re)[N], float (&im)[N], int t) {
 #pragma unroll
-    for (int k = 0; k < N; k += 4) {
-      const float4 hr = make_float4(to_tf32(re[k]), to_tf32(re[k + 1]), to_tf32(re[k + 2]), to_tf32(re[k + 3]));
-      const float4 hi = make_float4(to_tf32(im[k]), to_tf32(im[k + 1]), to_tf32(im[k + 2]), to_tf32(im[k + 3]));
-      *reinterpret_cast<float4*>(A + kmajor<K>(t, k)) = hr;
-      *reinterpret_cast<float4*>(A + kmajor<K>(t, N + k)) = hi;
-      if constexpr (TC == kTc3xTF32) {
-        float* Al = A + 128 * K;
-        *reinterpret_cast<float4*>(Al + kmajor<K>(t, k)) =
-            make_float4(to_tf32(re[k] - hr.x), to_tf32(re[k + 1] - hr.y), to_tf32(re[k + 2] - hr.z),
-                        to_tf32(re[k + 3] - hr.w));
-        *reinterpret_cast<float4*>(Al + kmajor<K>(t, N + k)) =
-            make_float4(to_tf32(im[k] - hi.x), to_tf32(im[k + 1] - hi.y), to_tf32(im[k + 2] - hi.z),
-                        to_tf32(im[k + 3] - hi.w));
-      }
+    for (int k = 0; k < N; k += 8) {
+      put8(t, k, re + k);
+      put8(t, N + k, im + k);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -332,9 +383,9 @@ struct TcDft {
     if (t == 0) {
       const uint32_t a0 = smem_u32(A), w0 = smem_u32(W);
       mma_set(a0, w0, true);
-      if constexpr (TC == kTc3xTF32) {
-        mma_set(a0, w0 + K * K * 4, false);        // Ah Wl
-        mma_set(a0 + 128 * K * 4, w0, false);      // Al Wh
+      if constexpr (kSplit) {
+        mma_set(a0, w0 + K * K * ES, false);        // Ah Wl
+        mma_set(a0 + 128 * K * ES, w0, false);      // Al Wh
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(mbar))
@@ -424,8 +475,8 @@ collide_kernel(const CollideArgs args) {
   // tensor-core transforms: TMEM accumulator (2N columns), completion barrier, DFT matrix
   TcDft<N, TC> tc;
   if constexpr (TC != kTcNone) {
-    tc.A = reinterpret_cast<float*>(smem_raw + Cfg::OFF_TCA);
-    tc.W = reinterpret_cast<const float*>(smem_raw + Cfg::OFF_TCW);
+    tc.A = smem_raw + Cfg::OFF_TCA;
+    tc.W = smem_raw + Cfg::OFF_TCW;
     tc.mbar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::OFF_TCB);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TCB + 8);
     if ((threadIdx.x >> 5) == 0) {
@@ -437,7 +488,7 @@ collide_kernel(const CollideArgs args) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tc.mbar)));
       asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    TcDft<N, TC>::build_w(reinterpret_cast<float*>(smem_raw + Cfg::OFF_TCW), threadIdx.x, Cfg::THREADS);
+    TcDft<N, TC>::build_w(smem_raw + Cfg::OFF_TCW, threadIdx.x, Cfg::THREADS);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1019,6 +1070,7 @@ struct PlaneCfg {
   static constexpr int THREADS = CPB * N;
   static constexpr size_t SMEM = (size_t)CPB * CELL_SMEM;
   static_assert(CPB >= 1, "one cell must fit");
+  static_assert(N <= 32 || CPB <= 15, "one named barrier per cell (ids 1..15)");
   static_assert((2 * BUF * sizeof(T2)) % 16 == 0 || true, "");
 };
 
@@ -1030,6 +1082,16 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
   constexpr int n = N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int ci = threadIdx.x / N, t = threadIdx.x % N;
+  // The cell's threads synchronise among themselves only: the lanes of one warp for
+  // N <= 32, a named barrier (id 1 + cell) of its 64 threads for N = 64.
+  auto cell_sync = [&]() {
+    if constexpr (N <= 32) {
+      const unsigned lanes = (N == 32) ? 0xffffffffu : (((1u << N) - 1u) << ((threadIdx.x & 31) / N * N));
+      __syncwarp(lanes);
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + ci), "r"(N) : "memory");
+    }
+  };
   unsigned char* base = smem_raw + (size_t)ci * Cfg::CELL_SMEM;
   T2* Fh = reinterpret_cast<T2*>(base);                 // spectrum [kx][ky]
   T2* P = Fh + Cfg::BUF;                                 // plane buffer [x][ky]
@@ -1067,7 +1129,7 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
   fft_regs<N, -1>(re, im);
 #pragma unroll
   for (int k = 0; k < N; ++k) P[t * RW_ + k] = mk2<T>(re[k], im[k]);
-  __syncthreads();
+  cell_sync();
 #pragma unroll
   for (int x = 0; x < N; ++x) {
     const T2 v = P[x * RW_ + t];
@@ -1085,7 +1147,7 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
   }
 #pragma unroll
   for (int y = 0; y < N; ++y) acc[y] = T(0);
-  __syncthreads();
+  cell_sync();
 
   for (int j = 0; j <= M_eff; ++j) {
     const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
@@ -1100,7 +1162,7 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
     fft_regs<N, +1>(re, im);
 #pragma unroll
     for (int x = 0; x < N; ++x) P[x * RW_ + t] = mk2<T>(re[x], im[x]);
-    __syncthreads();
+    cell_sync();
 #pragma unroll
     for (int ky = 0; ky < N; ++ky) {
       const T2 v = P[t * RW_ + ky];
@@ -1112,7 +1174,7 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
 #pragma unroll
       for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
     }
-    __syncthreads();  // the next term overwrites P
+    cell_sync();  // the next term overwrites P
   }
   // re[] holds the loss multiplier L along y of row x = t
 
@@ -1149,14 +1211,14 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
     r[8] = 0.0;
     r[9] = 0.5 * ((vx * vx + L * L) * s0 - 2.0 * L * dv * s1 + dv * dv * s2);
   }
-  __syncthreads();
+  cell_sync();
   double* tot = red + N * 10;
   if (t < 10) {
     double v = 0.0;
     for (int q = 0; q < N; ++q) v += red[q * 10 + t];
     tot[t] = v;
   }
-  __syncthreads();
+  cell_sync();
   double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (args.project) {
     double tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};

@@ -19,6 +19,9 @@ boltz_status dispatch_3d_tc(const boltz_grid_s* g, const CollideArgs& a, int64_t
                             int f_is_fp64) {
   if (prec == BOLTZ_TF32_DFT)
     return f_is_fp64 ? dispatch_tc<double, kTcTF32>(g, a, n_cells, st) : dispatch_tc<float, kTcTF32>(g, a, n_cells, st);
+  if (prec == BOLTZ_3XBF16_DFT)
+    return f_is_fp64 ? dispatch_tc<double, kTc3xBF16>(g, a, n_cells, st)
+                     : dispatch_tc<float, kTc3xBF16>(g, a, n_cells, st);
   return f_is_fp64 ? dispatch_tc<double, kTc3xTF32>(g, a, n_cells, st) : dispatch_tc<float, kTc3xTF32>(g, a, n_cells, st);
 }
 
