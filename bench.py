@@ -551,6 +551,7 @@ def run_ours(args, wl):
             dist.barrier()
         torch.cuda.synchronize()
 
+    nvtx = torch.cuda.nvtx  # phase ranges for nsight timelines; no effect otherwise
     # ---- device-resident timing --------------------------------------------------------
     for _ in range(args.warmup):
         B.boltz_relax(batch, f, wl["dt"], 1, rk, stream)
@@ -564,6 +565,7 @@ def run_ours(args, wl):
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     barrier()
+    nvtx.range_push("timed steps")
     t_start.record(stream)
     for k in range(args.steps):
         if flush is not None:
@@ -573,6 +575,7 @@ def run_ours(args, wl):
         ev[k][1].record(stream)
     t_end.record(stream)
     barrier()
+    nvtx.range_pop()
     clocks = sampler.stop()
     B.boltz_stream_status(stream)
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -593,6 +596,7 @@ def run_ours(args, wl):
     drift = ((U1 - U0).abs() / scale).max(dim=0).values.cpu().tolist()
 
     # ---- end to end through the public API with host buffers ----------------------------
+    nvtx.range_push("end to end")
     # boltz_relax_host: every step uploads f from pinned host memory, runs the step and
     # downloads the result, copies pipelined with the compute chunk by chunk
     out_host = torch.empty_like(host).pin_memory()
@@ -607,6 +611,7 @@ def run_ours(args, wl):
     e1.record(stream)
     barrier()
     B.boltz_stream_status(stream)
+    nvtx.range_pop()
     e2e_ms = e0.elapsed_time(e1)
     e2e_ms = max_over_ranks(e2e_ms, "cuda")
     e2e_value = cells * ws * e2e_steps * rk / (e2e_ms / 1000.0)

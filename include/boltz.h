@@ -284,6 +284,12 @@ boltz_status boltz_server_submit(boltz_server s, int grid_index, const float* f_
 boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued);
 boltz_status boltz_server_pump(boltz_server s, int* n_resident, int* n_queued, int* n_launched);
 boltz_status boltz_server_poll(boltz_server s, int64_t job_id, int* done);
+/* Checkpoint of one job: f_host (N^3 floats) receives the job's state after every
+ * iteration issued for it so far, *remaining_steps the steps still to run (0 once
+ * finished).  Synchronises the job's grid stream.  The state plus the remaining steps is
+ * all a job needs: submitting them to any server with the same grid continues the job
+ * and gives the same bits as an uninterrupted run. */
+boltz_status boltz_server_checkpoint(boltz_server s, int64_t job_id, float* f_host, int* remaining_steps);
 boltz_status boltz_server_destroy(boltz_server s);
 
 /* U[c] = (rho, rho u, E) of every cell (Eq. i5 on the grid, Eq. DM), float64,

@@ -37,7 +37,7 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
             "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
             "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
-            "boltz_server_pump", "boltz_create_grid2d")
+            "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint")
 
 
 class BoltzError(RuntimeError):
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_server_submit.argtypes = [vp, i32, vp, vp, i32, P(i64)]
         L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
         L.boltz_server_pump.argtypes = [vp, P(i32), P(i32), P(i32)]
+        L.boltz_server_checkpoint.argtypes = [vp, i64, vp, P(i32)]
         L.boltz_server_poll.argtypes = [vp, i64, P(i32)]
         L.boltz_server_destroy.argtypes = [vp]
         L.boltz_stream_status.argtypes = [vp]
@@ -112,7 +113,7 @@ def lib() -> ctypes.CDLL:
                      "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
                      "boltz_server_destroy", "boltz_relax_host", "boltz_plan_create", "boltz_plan_run",
                      "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump",
-                     "boltz_create_grid2d"):
+                     "boltz_create_grid2d", "boltz_server_checkpoint"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -264,6 +265,12 @@ class Server:
         r, q, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().boltz_server_pump(self.handle, ctypes.byref(r), ctypes.byref(q), ctypes.byref(n)))
         return r.value, q.value, n.value
+
+    def checkpoint(self, job_id: int, f_host) -> int:
+        """Copy the job's current state into f_host; returns the steps still to run."""
+        r = ctypes.c_int()
+        _check(lib().boltz_server_checkpoint(self.handle, job_id, _ptr(f_host), ctypes.byref(r)))
+        return r.value
 
     def poll(self, job_id: int) -> bool:
         d = ctypes.c_int()

@@ -317,6 +317,7 @@ boltz_status boltz_relax_indexed(const boltz_batch* b, void* f, const int64_t* c
     g->U0 = nullptr;
     g->U0_cap = 0;
     if (cudaMalloc(&g->U0, (size_t)pool_cells * 5 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for later launches
       set_error("relax scratch allocation failed");
       return BOLTZ_ENOMEM;
     }
@@ -379,6 +380,7 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
     g->U0 = nullptr;
     g->U0_cap = 0;
     if (cudaMalloc(&g->U0, (size_t)b->n_cells * 5 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for later launches
       set_error("relax scratch allocation failed");
       return BOLTZ_ENOMEM;
     }
@@ -391,6 +393,7 @@ boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, in
     g->stage = nullptr;
     g->stage_cap = 0;
     if (cudaMalloc(&g->stage, stage_bytes) != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for later launches
       set_error("relax scratch allocation failed");
       return BOLTZ_ENOMEM;
     }

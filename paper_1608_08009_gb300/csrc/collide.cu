@@ -180,14 +180,17 @@ boltz_status upload_tables(boltz_grid_s* g) {
           h32[dst] = make_float2((float)a, (float)b);
         }
   if (want64 && (e = cudaMalloc(&g->tab64, entries * sizeof(double2))) != cudaSuccess) {
+    cudaGetLastError();  // not sticky: clear it for later launches
     set_error(std::string("device tables: ") + cudaGetErrorString(e));
     return BOLTZ_ENOMEM;
   }
   if ((e = cudaMalloc(&g->tab32, entries * sizeof(float2))) != cudaSuccess) {
+    cudaGetLastError();  // not sticky: clear it for later launches
     set_error(std::string("device tables: ") + cudaGetErrorString(e));
     return BOLTZ_ENOMEM;
   }
   if ((e = cudaMalloc(&g->w_dev, (size_t)std::max(1, g->M_eff) * sizeof(double))) != cudaSuccess) {
+    cudaGetLastError();  // not sticky: clear it for later launches
     set_error(std::string("device tables: ") + cudaGetErrorString(e));
     return BOLTZ_ENOMEM;
   }

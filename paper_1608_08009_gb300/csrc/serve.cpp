@@ -138,6 +138,7 @@ boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec,
     cudaError_t e;
     if ((e = cudaMalloc(&p.f, (size_t)p.capacity * p.slot_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&p.idx_dev, (size_t)p.capacity * sizeof(int64_t))) != cudaSuccess) {
+      cudaGetLastError();  // an allocation failure is not sticky: clear it for later launches
       free_server(s);
       set_error(std::string("server pool allocation: ") + cudaGetErrorString(e));
       return BOLTZ_ENOMEM;
@@ -145,6 +146,7 @@ boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec,
     for (int b = 0; b < kIdxBufs; ++b) {
       if ((e = cudaMallocHost(&p.idx_host[b], (size_t)p.capacity * sizeof(int64_t))) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&p.idx_ready[b], cudaEventDisableTiming)) != cudaSuccess) {
+        cudaGetLastError();
         free_server(s);
         set_error(std::string("server host buffers: ") + cudaGetErrorString(e));
         return BOLTZ_ENOMEM;
@@ -303,6 +305,29 @@ boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued) {
 
 boltz_status boltz_server_pump(boltz_server s, int* n_resident, int* n_queued, int* n_launched) {
   return advance(s, false, n_resident, n_queued, n_launched);
+}
+
+boltz_status boltz_server_checkpoint(boltz_server s, int64_t job_id, float* f_host, int* remaining_steps) {
+  if (!s || !f_host || !remaining_steps || job_id < 0 || job_id >= (int64_t)s->jobs.size()) {
+    set_error("bad checkpoint arguments");
+    return BOLTZ_EINVAL;
+  }
+  Job& j = s->jobs[job_id];
+  Pool& p = s->pools[j.grid];
+  cudaError_t e;
+  if (j.state == 0) {  // still queued: its state is the submitted one
+    std::memcpy(f_host, j.in, p.slot_bytes);
+  } else if (j.state == 1) {  // resident: the state after the iterations issued so far
+    if ((e = cudaMemcpyAsync(f_host, p.f + (size_t)j.slot * p.n, p.slot_bytes, cudaMemcpyDeviceToHost, p.stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(p.stream)) != cudaSuccess)
+      return cuda_err(e, "checkpoint copy");
+  } else {  // finished or copying out: the result
+    if ((e = cudaEventSynchronize(j.done)) != cudaSuccess) return cuda_err(e, "checkpoint wait");
+    std::memcpy(f_host, j.out, p.slot_bytes);
+  }
+  *remaining_steps = (j.state >= 2) ? 0 : j.remaining;
+  return BOLTZ_OK;
 }
 
 boltz_status boltz_server_poll(boltz_server s, int64_t job_id, int* done) {

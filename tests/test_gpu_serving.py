@@ -111,3 +111,38 @@ def test_pump_gives_the_same_results_as_step():
     s2.close()
     for o, r, (_, f, _) in zip(outs, ref, jobs):
         assert np.array_equal(o.numpy().reshape(f.shape), r)
+
+
+def test_checkpoint_and_resume_on_another_server():
+    """A job stopped after some iterations and resubmitted (its state and remaining steps)
+    to a new server finishes with the same bits as the uninterrupted run."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g32 = B.Grid(32, 8.0, 1.0, 16)
+    f = W.two_maxwellians(1, 32, 8.0, seed=17)[0]
+    ref = _run(B.Server([g32], B.BOLTZ_FP32_FFT, DT, 1 << 26), [(0, f, 9)], [0])[0]
+    s1 = B.Server([g32], B.BOLTZ_FP32_FFT, DT, 1 << 26)
+    out = torch.empty(f.size, dtype=torch.float32).pin_memory()
+    j = s1.submit(0, _pinned(f.ravel()), out, 9)
+    for _ in range(4):
+        s1.step()
+    state = torch.empty(f.size, dtype=torch.float32).pin_memory()
+    left = s1.checkpoint(j, state)
+    assert left == 5
+    s1.close()
+    s2 = B.Server([g32], B.BOLTZ_FP32_FFT, DT, 1 << 26)
+    res = _run(s2, [(0, state.numpy().reshape(f.shape), left)], [0])[0]
+    s2.close()
+    assert np.array_equal(res, ref)
+    g32.close()
+
+
+def test_server_allocation_failure_is_reported():
+    """A pool that cannot be allocated (a 16 TiB budget) returns BOLTZ_ENOMEM, no crash."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g16 = B.Grid(16, 6.0, 1.0, 8)
+    with pytest.raises(B.BoltzError) as ei:
+        B.Server([g16], B.BOLTZ_FP32_FFT, DT, 16 << 40)
+    assert ei.value.status == B.BOLTZ_ENOMEM
+    g16.close()
