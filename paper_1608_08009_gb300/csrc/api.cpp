@@ -240,7 +240,6 @@ boltz_status boltz_destroy_grid(boltz_grid g) {
   cudaFree(g->U0);
   cudaFree(g->stage);
   cudaFree(g->split_buf);
-  cudaFree(g->spec_buf);
   boltz::free_host_pipeline(g);
   if (prev >= 0) cudaSetDevice(prev);
   delete g;

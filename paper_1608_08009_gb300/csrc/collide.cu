@@ -327,23 +327,6 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
     boltz_status r = ensure_split_scratch(g, n_cells, G, prec, stream);
     if (r != BOLTZ_OK) return r;
   }
-  if (g->N > 32) {
-    // spectrum pencils of the large-N kernel: [cells][G][n] float2
-    const size_t need = (size_t)n_cells * G * n * sizeof(float2);
-    if (need > g->spec_cap) {
-      cudaError_t e = cudaStreamSynchronize(stream);
-      if (e != cudaSuccess) return cuda_fail(e, "spectrum scratch sync");
-      cudaFree(g->spec_buf);
-      g->spec_buf = nullptr;
-      g->spec_cap = 0;
-      if (cudaMalloc(&g->spec_buf, need) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("spectrum scratch allocation failed");
-        return BOLTZ_ENOMEM;
-      }
-      g->spec_cap = need;
-    }
-  }
   CollideArgs args;
   args.f_in = f_in;
   args.f_base = f_base;
@@ -366,7 +349,6 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.arrivals = (G > 1) ? reinterpret_cast<unsigned*>(sb) : nullptr;
   args.part = (G > 1) ? sb + cnt_bytes : nullptr;
   args.loss = (G > 1) ? sb + cnt_bytes + (size_t)n_cells * G * n * tsz : nullptr;
-  args.spec = g->spec_buf;
   if (prec == BOLTZ_FP64) {
     args.tab = g->tab64;
     return dispatch_3d_f64(g, args, n_cells, stream, cluster, f_is_fp64);

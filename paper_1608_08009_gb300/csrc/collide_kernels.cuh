@@ -780,12 +780,30 @@ collide_kernel(const CollideArgs args) {
 // ------------------------------------------------------------------------------------
 // N = 48 and 64 (float32).  One pencil of 48 or 64 complex values takes 96 or 128
 // registers, so the gain accumulator and the spectrum cannot stay in registers as above:
-// the spectrum pencils go to global scratch (each thread reads back only its own pencil:
-// coalesced along kz, L2-resident), the gain accumulator of the CTA's x-slab lives in
-// shared memory, and one x-plane buffer serves every term (two cluster barriers per
-// term).  The epilogue recomputes g in a second sweep instead of keeping N float64 values
+// each thread's spectrum pencil goes to tensor memory (TMEM, 256 KB per SM, unused by
+// this kernel otherwise; written once, read back by the same thread every term), the
+// gain accumulator of the CTA's x-slab lives in shared memory, and one x-plane buffer
+// serves every term (two cluster barriers per term).  The epilogue recomputes g in a second sweep instead of keeping N float64 values
 // per thread.  Otherwise the same decomposition and arithmetic as collide_kernel.
 // ------------------------------------------------------------------------------------
+// 16 consecutive 32-bit TMEM columns of this thread's lane <-> registers (tcgen05 32x32b)
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          addr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+      : "r"(addr)
+      : "memory");
+}
+
 template <int N, int C>
 struct LargeCfg {
   static constexpr int NP = N / C;
@@ -799,7 +817,14 @@ struct LargeCfg {
   static constexpr size_t OFF_ACC = XB * sizeof(float2);
   static constexpr size_t OFF_RED = OFF_ACC + ACC * sizeof(float);
   static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
-  static constexpr size_t SMEM = OFF_FLAG + 16;
+  static constexpr size_t SMEM = OFF_FLAG + 16;  // flag, then the TMEM address
+  // spectrum pencils in TMEM: warp w uses lanes 32 (w % 4) .. + 31 and the column group
+  // w / 4 of 2N columns (N real parts, then N imaginary parts)
+  static constexpr int TMEM_NEED = ((WARPS + 3) / 4) * 2 * N;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128
+                                   : TMEM_NEED <= 256 ? 256 : 512;
+  static_assert(TMEM_NEED <= 512, "spectrum slab fits TMEM");
+  static_assert((2 * N) % 16 == 0, "whole 16-column TMEM chunks");
   static_assert(THREADS % 32 == 0 && NP % VEC == 0, "whole warps and chunks");
   static_assert(OFF_RED % 16 == 0, "aligned reduction area");
   static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -846,8 +871,19 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   const int M_eff = args.M_eff;
   const int ky_own = rank * NP + kyl;
   const int x_own = rank * NP + xlt;
-  // this thread's spectrum pencil (its (ky, kz), all kx) in global scratch
-  T2* spec = reinterpret_cast<T2*>(args.spec) + ((size_t)lc * G + gi) * n + (size_t)ky_own * N * N + kzt;
+  // this thread's spectrum pencil (its (ky, kz), all kx) in TMEM, written once by the
+  // forward x pass and read back in every kx pass
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_FLAG + 8);
+  if ((t >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(Cfg::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t spec_addr = tmem_base + ((uint32_t)(32 * ((t >> 5) & 3)) << 16) + (uint32_t)((t >> 7) * 2 * N);
 
   T re[N], im[N];
   const double L = args.geom.L, dv = args.geom.dv;
@@ -914,8 +950,15 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
       const bool z0 = nyq || (kx == N / 2);
-      spec[(size_t)kx * N] = z0 ? make_float2(0.f, 0.f) : make_float2(re[kx] * scale, im[kx] * scale);
+      re[kx] = z0 ? 0.f : re[kx] * scale;
+      im[kx] = z0 ? 0.f : im[kx] * scale;
     }
+#pragma unroll
+    for (int c = 0; c < N; c += 16) {
+      tmem_st16(spec_addr + c, re + c);
+      tmem_st16(spec_addr + N + c, im + c);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   for (int i = t; i < (int)Cfg::ACC; i += Cfg::THREADS) accs[i] = 0.f;
   cluster_barrier<C>();  // peers done gathering from this CTA's buffer
@@ -931,11 +974,17 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
     {  // kx pass with the coefficients: thread (kyl, kz); outputs scattered by x
       const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
 #pragma unroll
+      for (int c = 0; c < N; c += 16) {
+        tmem_ld16(spec_addr + c, re + c);
+        tmem_ld16(spec_addr + N + c, im + c);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
       for (int kx = 0; kx < N; ++kx) {
-        const T2 c = spec[(size_t)kx * N];
+        const float cr = re[kx], cim = im[kx];
         const T2 ab = __ldg(tj + kx * N);
-        re[kx] = ab.x * c.x - ab.y * c.y;
-        im[kx] = ab.x * c.y + ab.y * c.x;
+        re[kx] = ab.x * cr - ab.y * cim;
+        im[kx] = ab.x * cim + ab.y * cr;
       }
       fft_regs<N, +1>(re, im);
 #pragma unroll
@@ -976,6 +1025,12 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
     }
     if (i < nt - 1) cluster_barrier<C>();  // owners done reading before the next scatter
   }
+
+  // the spectrum is no longer needed: free the TMEM columns
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((t >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(Cfg::TMEM_COLS));
 
   const int x = x_own, z = zt;
   float* acc_row = accs + (size_t)xlt * N * N + z;  // acc_row[y * N], this thread's (x, z) row

@@ -48,7 +48,6 @@ struct CollideArgs {
   void* part;          // [cells][G][n] T
   void* loss;          // [cells][n] T
   unsigned* arrivals;  // [cells], zero between launches
-  void* spec;          // N = 48, 64: spectrum pencils [cells][G][ky][kx][kz] float2
   KernelGeom geom;
 };
 
@@ -78,9 +77,6 @@ struct boltz_grid_s {
   // partial gains and loss of split launches (term_groups > 1), grown on demand
   mutable void* split_buf = nullptr;
   mutable size_t split_cap = 0;  // bytes
-  // spectrum pencils of the N = 48, 64 kernel, grown on demand
-  mutable void* spec_buf = nullptr;
-  mutable size_t spec_cap = 0;  // bytes
   // resources of boltz_relax_host (host_io.cpp), created on first use
   static constexpr int kHostBufs = 3;
   void* hbuf[kHostBufs] = {nullptr, nullptr, nullptr};  // device staging, one chunk each
