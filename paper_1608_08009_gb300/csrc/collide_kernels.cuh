@@ -68,20 +68,32 @@ struct CollideCfg {
   static constexpr int NP = N / C;          // slab width (x for physical, ky for spectral)
   static constexpr int THREADS = NP * N;    // one pencil per thread in every pass
   static constexpr int WARPS = THREADS / 32;
-  // CTAs per SM asked of the register allocator.  float32 32^3 with C = 8: 3 (168
-  // registers, 44 bytes spilled outside the term loop) runs 11 % faster on GB300 than the
-  // 252-register 2-CTA version: twelve warps hide the table loads and barrier waits.
+  // CTAs per SM asked of the register allocator.  float32 32^3 with C = 8: 4 (128
+  // registers; the spectrum pencil is in TMEM and the x-plane buffer single, 34 KB of
+  // shared memory): sixteen warps per SM hide the table loads and barrier waits.  On
+  // GB300: 2 CTAs (252 registers) 131k, 3 CTAs (168 registers, double buffer) 147k,
+  // 4 CTAs 161k cell-collisions/s.
+  static constexpr bool kQuad = (sizeof(T) == 4 && N == 32 && C == 8 && TC == kTcNone);
   static constexpr int MIN_BLOCKS = (TC == kTcTF32 || TC == kTc3xBF16) ? 2
                                     : (TC == kTc3xTF32)                  ? 1
-                                    : (sizeof(T) == 4 && N == 32 && C == 8) ? 3
-                                                                            : 1;
+                                    : kQuad                              ? 4
+                                                                         : 1;
   using T2 = typename Vec2<T>::type;
   static constexpr bool kF32 = sizeof(T) == 4;
-  // float32: the spectrum pencil of each thread stays in registers and the x-plane
-  // buffer is double-buffered (one cluster barrier per direction); float64 (register
-  // bound) keeps the spectrum in shared memory with a single x-plane buffer.
+  // float32: the spectrum pencil of each thread is private to it (TMEM at N = 16, 32,
+  // registers otherwise) and the x-plane buffer is double-buffered (one cluster barrier
+  // per term) except in the 4-CTA 32^3 configuration, which trades the second buffer for
+  // occupancy; float64 (register bound) keeps the spectrum in shared memory with a single
+  // x-plane buffer.
   static constexpr bool kRegSpec = kF32;
-  static constexpr int NXB = (kRegSpec && TC == kTcNone) ? 2 : 1;
+  static constexpr int NXB = (kRegSpec && TC == kTcNone && !kQuad) ? 2 : 1;
+  // float32 register-FFT path: the spectrum pencil of each thread lives in TMEM (warp w:
+  // lanes 32 (w % 4) .., column group w / 4 of 2N columns) instead of 2N registers
+  // (N = 16, 32: the pencil's real and imaginary halves are whole 16-column chunks)
+  static constexpr bool kTmemSpec = kF32 && TC == kTcNone && N % 16 == 0;
+  static constexpr int TMEM_NEED = ((THREADS / 32 + 3) / 4) * 2 * N;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128
+                                   : TMEM_NEED <= 256 ? 256 : 512;
   // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
   // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
   // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
@@ -240,6 +252,24 @@ __device__ __forceinline__ void cluster_correction(const CollideArgs& args, cons
     }
   }
   cluster_barrier<C>();  // no CTA leaves while a peer may still read its partial sums
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane <-> registers (tcgen05 32x32b)
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          addr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+      : "r"(addr)
+      : "memory");
 }
 
 // ---- tensor-core 1D DFT of 128 pencils (tcgen05) ------------------------------------
@@ -470,7 +500,23 @@ collide_kernel(const CollideArgs args) {
   const int x_own = rank * NP + xlt;   // physical x of this thread's rows
 
   T re[N], im[N];
-  T fr[kRegSpec ? N : 1], fi[kRegSpec ? N : 1];  // spectrum pencil (kRegSpec)
+  constexpr bool kTmemSpec = Cfg::kTmemSpec;
+  constexpr bool kRegArr = kRegSpec && !kTmemSpec;
+  T fr[kRegArr ? N : 1], fi[kRegArr ? N : 1];  // spectrum pencil in registers (tensor-core modes)
+  uint32_t spec_addr = 0, spec_tmem = 0;          // spectrum pencil in TMEM (register-FFT float32)
+  if constexpr (kTmemSpec) {
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_FLAG + 8);
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                   "r"(Cfg::TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    spec_tmem = *slot;
+    spec_addr = spec_tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + (uint32_t)((threadIdx.x >> 7) * 2 * N);
+  }
 
   // tensor-core transforms: TMEM accumulator (2N columns), completion barrier, DFT matrix
   TcDft<N, TC> tc;
@@ -579,12 +625,23 @@ collide_kernel(const CollideArgs args) {
       // Every mode with a component -N/2 is removed so each inverse transform is real.
       const bool z0 = nyq || (kx == N / 2);
       const T vr = z0 ? T(0) : re[kx] * scale, vi = z0 ? T(0) : im[kx] * scale;
-      if constexpr (kRegSpec) {
+      if constexpr (kTmemSpec) {
+        re[kx] = vr;
+        im[kx] = vi;
+      } else if constexpr (kRegSpec) {
         fr[kx] = vr;
         fi[kx] = vi;
       } else {
         Fh[(kx * NP + kyl) * N + kzt] = mk2<T>(vr, vi);
       }
+    }
+    if constexpr (kTmemSpec) {
+#pragma unroll
+      for (int c = 0; c < N; c += 16) {
+        tmem_st16(spec_addr + c, reinterpret_cast<const float*>(re) + c);
+        tmem_st16(spec_addr + N + c, reinterpret_cast<const float*>(im) + c);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
   }
   if constexpr (Cfg::NXB == 1) cluster_barrier<C>();  // single buffer: peers done reading it
@@ -598,10 +655,20 @@ collide_kernel(const CollideArgs args) {
   // outputs x = q NP + c VEC + (0 .. VEC-1) go to chunk c of CTA q at (ky, kz)
   auto pass_kx = [&](int j, T2* XB) {
     const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
+    if constexpr (kTmemSpec) {
+#pragma unroll
+      for (int c = 0; c < N; c += 16) {
+        tmem_ld16(spec_addr + c, reinterpret_cast<float*>(re) + c);
+        tmem_ld16(spec_addr + N + c, reinterpret_cast<float*>(im) + c);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    }
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
       T2 c;
-      if constexpr (kRegSpec) {
+      if constexpr (kTmemSpec) {
+        c = mk2<T>(re[kx], im[kx]);
+      } else if constexpr (kRegSpec) {
         c = mk2<T>(fr[kx], fi[kx]);
       } else {
         c = Fh[(kx * NP + kyl) * N + kzt];
@@ -695,6 +762,13 @@ collide_kernel(const CollideArgs args) {
     }
   }
 
+  if constexpr (kTmemSpec) {
+    // the spectrum is no longer needed: free its TMEM columns
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(spec_tmem), "r"(Cfg::TMEM_COLS));
+  }
   if constexpr (TC != kTcNone) {
     // every thread has read its last accumulator row: free the TMEM columns
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -786,24 +860,6 @@ collide_kernel(const CollideArgs args) {
 // serves every term (two cluster barriers per term).  The epilogue recomputes g in a second sweep instead of keeping N float64 values
 // per thread.  Otherwise the same decomposition and arithmetic as collide_kernel.
 // ------------------------------------------------------------------------------------
-// 16 consecutive 32-bit TMEM columns of this thread's lane <-> registers (tcgen05 32x32b)
-__device__ __forceinline__ void tmem_st16(uint32_t addr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          addr),
-      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
-      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
-        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
-      : "r"(addr)
-      : "memory");
-}
-
 template <int N, int C>
 struct LargeCfg {
   static constexpr int NP = N / C;
