@@ -141,6 +141,20 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
+// Cluster barrier that only separates this CTA's reads of its own shared memory from
+// the peers' next writes into it (write-after-read): nothing is published, so the
+// arrive needs no release fence.  Every value read before it has been consumed by the
+// instructions ahead of the arrive (in-order issue, scoreboarded loads), so no read can
+// still be pending when a peer passes the wait.
+template <int C>
+__device__ __forceinline__ void cluster_barrier_war() {
+  if constexpr (C > 1) {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
 template <int C, typename P>
 __device__ __forceinline__ P* cta_smem(P* p, int r) {
   if constexpr (C > 1) {
@@ -758,7 +772,7 @@ collide_kernel(const CollideArgs args) {
       pass_kz(XB0);
       __syncthreads();
       pass_ky(XB0, wj, j < M_eff);
-      if (i < nt - 1) cluster_barrier<C>();  // single buffer: owners done before the next scatter
+      if (i < nt - 1) cluster_barrier_war<C>();  // single buffer: owners done before the next scatter
     }
   }
 
@@ -1079,7 +1093,7 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
         for (int y = 0; y < N; ++y) a[y * N] += wj * (re[y] * im[y]);
       }
     }
-    if (i < nt - 1) cluster_barrier<C>();  // owners done reading before the next scatter
+    if (i < nt - 1) cluster_barrier_war<C>();  // owners done reading before the next scatter
   }
 
   // the spectrum is no longer needed: free the TMEM columns
