@@ -58,7 +58,7 @@ template <> __device__ __forceinline__ double2 mk2<double>(double a, double b) {
 // Status bits of g_boltz_status.
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusBadIndex = 4u;
-constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on a tensor-core barrier gave up
+constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on an mbarrier gave up
 
 // Tensor-core transform modes of the float32 path (0: register FFT).
 constexpr int kTcNone = 0, kTcTF32 = 1, kTc3xBF16 = 2, kTc3xTF32 = 3;
@@ -121,7 +121,11 @@ struct CollideCfg {
   static constexpr size_t OFF_TCW = OFF_TCA + TCA_BYTES;
   static constexpr size_t TCW_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * TC_K * TC_K * TC_ES : 0;
   static constexpr size_t OFF_TCB = OFF_TCW + TCW_BYTES;  // mbarrier (8 B) + TMEM address (4 B)
-  static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 16;
+  // 32^3 4-CTA configuration: the kx-pass scatter uses st.async, which signals the
+  // owner's mbarrier (at OFF_FLAG + 16) with the bytes it delivers
+  static constexpr bool kAsyncScatter = kQuad && C > 1;
+  static constexpr uint32_t SCATTER_BYTES = (uint32_t)NP * N * N * 2 * sizeof(T);  // received per term
+  static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 24;
   static_assert(TC == kTcNone || (kF32 && THREADS == 128), "tensor-core transforms: float32, 128 pencils per CTA");
   static_assert(THREADS % 32 == 0, "whole warps");
   static_assert(NP % VEC == 0, "whole chunks");
@@ -188,6 +192,30 @@ __device__ __forceinline__ void st_cluster_chunk(uint32_t a, const float* re, co
 }
 __device__ __forceinline__ void st_cluster_chunk(uint32_t a, const double* re, const double* im) {
   asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" :: "r"(a), "d"(re[0]), "d"(im[0]) : "memory");
+}
+// One 16-byte chunk to a peer's shared memory with st.async: the store completes a
+// transaction of 16 bytes on the peer's mbarrier (both addresses shared::cluster).
+__device__ __forceinline__ void st_async_chunk(uint32_t a, const float* re, const float* im, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               :: "r"(a), "f"(re[0]), "f"(im[0]), "f"(re[1]), "f"(im[1]), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with parity `phase` of a local mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 20) && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+  }
+  return done != 0;
 }
 __device__ __forceinline__ void ld_cluster_chunk(uint32_t a, float* re, float* im) {
   asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -556,6 +584,19 @@ collide_kernel(const CollideArgs args) {
     tc.tmem = *tmem_slot;
     tc.phase = 0u;
   }
+  // asynchronous scatter (32^3, 4 CTAs per SM): the owner's mbarrier counts the bytes
+  // that reach its x-plane buffer; it is armed for term 0 before the barrier that ends
+  // the forward transform and re-armed for term i + 1 before the write-after-read
+  // barrier of term i, so no bytes of a term can arrive before their phase is armed
+  constexpr bool kAsync = Cfg::kAsyncScatter;
+  const uint32_t scat_mbar = smem_u32(smem_raw + Cfg::OFF_FLAG + 16);
+  uint32_t scat_phase = 0;
+  if constexpr (kAsync) {
+    if (threadIdx.x == 0) {
+      mbar_init(scat_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   // inverse 1D transform of this thread's pencil: register FFT or tensor-core DFT
   auto inverse_1d = [&]() {
     if constexpr (TC != kTcNone) {
@@ -658,6 +699,9 @@ collide_kernel(const CollideArgs args) {
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
   }
+  if constexpr (kAsync) {
+    if (threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
+  }
   if constexpr (Cfg::NXB == 1) cluster_barrier<C>();  // single buffer: peers done reading it
 
   // ---- angular loop: one complex inverse transform per separated term --------------
@@ -695,7 +739,13 @@ collide_kernel(const CollideArgs args) {
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
       T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
-      if constexpr (C > 1) {
+      if constexpr (kAsync) {
+        const uint32_t a = smem_u32(dst);
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+          st_async_chunk(cluster_addr(a, q), reinterpret_cast<const float*>(re) + q * NP + c * VEC,
+                         reinterpret_cast<const float*>(im) + q * NP + c * VEC, cluster_addr(scat_mbar, q));
+      } else if constexpr (C > 1) {
         const uint32_t a = smem_u32(dst);
 #pragma unroll
         for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
@@ -768,11 +818,22 @@ collide_kernel(const CollideArgs args) {
       const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
       const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
       pass_kx(j, XB0);
-      cluster_barrier<C>();
+      if constexpr (kAsync) {
+        // every producer's bytes of this term have landed in this CTA's buffer
+        if (!mbar_wait(scat_mbar, scat_phase)) atomicOr(&g_boltz_status, kStatusTimeout);
+        scat_phase ^= 1u;
+      } else {
+        cluster_barrier<C>();
+      }
       pass_kz(XB0);
       __syncthreads();
       pass_ky(XB0, wj, j < M_eff);
-      if (i < nt - 1) cluster_barrier_war<C>();  // single buffer: owners done before the next scatter
+      if (i < nt - 1) {
+        if constexpr (kAsync) {
+          if (threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
+        }
+        cluster_barrier_war<C>();  // single buffer: owners done before the next scatter
+      }
     }
   }
 
