@@ -34,8 +34,6 @@
 
 namespace boltz {
 
-constexpr int kTwiddles = 192;  // exp(2 pi i m / 192): the table of the register transforms
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -127,21 +125,12 @@ static boltz_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 boltz_status upload_tables(boltz_grid_s* g) {
-  // twiddles exp(2 pi i m / kTw), host libm in float64
-  double tc[kTwiddles], ts[kTwiddles];
-  float fc[kTwiddles], fs[kTwiddles];
-  for (int m = 0; m < kTwiddles; ++m) {
-    const double ang = 2.0 * 3.14159265358979323846 * m / (double)kTwiddles;
-    tc[m] = std::cos(ang);
-    ts[m] = std::sin(ang);
-    fc[m] = (float)tc[m];
-    fs[m] = (float)ts[m];
-  }
+  // twiddles of the register transforms, host libm in float64
+  TwiddleTables tw;
+  fill_twiddle_tables(tw);
   cudaError_t e;
-  if ((e = unit_upload_twiddles_f32(tc, ts, fc, fs)) != cudaSuccess ||
-      (e = unit_upload_twiddles_f64(tc, ts, fc, fs)) != cudaSuccess ||
-      (e = unit_upload_twiddles_tc(tc, ts, fc, fs)) != cudaSuccess ||
-      (e = unit_upload_twiddles_p2d(tc, ts, fc, fs)) != cudaSuccess)
+  if ((e = unit_upload_twiddles_f32(tw)) != cudaSuccess || (e = unit_upload_twiddles_f64(tw)) != cudaSuccess ||
+      (e = unit_upload_twiddles_tc(tw)) != cudaSuccess || (e = unit_upload_twiddles_p2d(tw)) != cudaSuccess)
     return cuda_fail(e, "twiddle upload");
 
   const size_t n = (g->dim == 2) ? (size_t)g->N * g->N : (size_t)g->N * g->N * g->N;

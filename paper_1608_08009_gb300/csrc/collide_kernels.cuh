@@ -1586,13 +1586,18 @@ static boltz_status launch2d_impl(const CollideArgs& a, int64_t n_cells, cudaStr
 
 // Per-unit services: the twiddle constants and the status word are per translation unit.
 #define BOLTZ_UNIT_SERVICES(TAG)                                                                  \
-  cudaError_t unit_upload_twiddles_##TAG(const double* tc, const double* ts, const float* fc,     \
-                                         const float* fs) {                                       \
+  cudaError_t unit_upload_twiddles_##TAG(const TwiddleTables& t) {                                 \
     cudaError_t e;                                                                                \
-    if ((e = cudaMemcpyToSymbol(c_twc64, tc, sizeof(double) * kTw)) != cudaSuccess) return e;     \
-    if ((e = cudaMemcpyToSymbol(c_tws64, ts, sizeof(double) * kTw)) != cudaSuccess) return e;     \
-    if ((e = cudaMemcpyToSymbol(c_twc32, fc, sizeof(float) * kTw)) != cudaSuccess) return e;      \
-    return cudaMemcpyToSymbol(c_tws32, fs, sizeof(float) * kTw);                                  \
+    if ((e = cudaMemcpyToSymbol(c_twc64, t.c64, sizeof(t.c64))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_tws64, t.s64, sizeof(t.s64))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_twl64, t.l64, sizeof(t.l64))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_twm64, t.m64, sizeof(t.m64))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_twr64, t.r64, sizeof(t.r64))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_twc32, t.c32, sizeof(t.c32))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_tws32, t.s32, sizeof(t.s32))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_twl32, t.l32, sizeof(t.l32))) != cudaSuccess) return e;        \
+    if ((e = cudaMemcpyToSymbol(c_twm32, t.m32, sizeof(t.m32))) != cudaSuccess) return e;        \
+    return cudaMemcpyToSymbol(c_twr32, t.r32, sizeof(t.r32));                                    \
   }                                                                                               \
   cudaError_t unit_read_clear_status_##TAG(unsigned* value) {                                     \
     unsigned v = 0, zero = 0;                                                                     \

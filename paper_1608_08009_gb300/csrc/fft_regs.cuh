@@ -7,13 +7,19 @@
 // exp(2 pi i m / 192) (192 = lcm of every stage length used) come from constant memory,
 // filled once per device by the host with the host libm cos/sin in float64 (and rounded
 // to float32 for the float32 path).
+//
+// The radix-4 stages use the factored twiddles of Linzer and Feig (IBM J. Res. Dev. 37,
+// 1993): w = lam i^e (1 + i mu) with |mu| <= 1, the quarter turn i^e a renaming and the
+// real factor lam carried into the following additions as fused multiply-adds.  A radix-4
+// butterfly with three non-trivial twiddles then costs 22 fused multiply-adds instead of
+// 12 multiplications/multiply-adds and 16 additions.
 #pragma once
 
 #include <cuda_runtime.h>
 
-namespace boltz {
+#include "twiddles.h"
 
-constexpr int kTw = 192;
+namespace boltz {
 
 // One copy per translation unit that includes this header (internal linkage); the host
 // fills every unit's copy through that unit's upload function.
@@ -21,6 +27,16 @@ static __constant__ double c_twc64[kTw];
 static __constant__ double c_tws64[kTw];
 static __constant__ float c_twc32[kTw];
 static __constant__ float c_tws32[kTw];
+// Factored twiddles, theta = 2 pi m / 192 (m not a multiple of 48): where
+// |cos theta| >= |sin theta|, lam = cos theta and mu = tan theta; otherwise
+// lam = sin theta and mu = cot theta.  rho[m] = lam[3m mod 192] / lam[m] (the radix-4
+// pair w, w^3).
+static __constant__ double c_twl64[kTw];
+static __constant__ double c_twm64[kTw];
+static __constant__ double c_twr64[kTw];
+static __constant__ float c_twl32[kTw];
+static __constant__ float c_twm32[kTw];
+static __constant__ float c_twr32[kTw];
 
 template <typename T> __device__ __forceinline__ T tw_cos(int m);
 template <typename T> __device__ __forceinline__ T tw_sin(int m);
@@ -28,6 +44,50 @@ template <> __device__ __forceinline__ double tw_cos<double>(int m) { return c_t
 template <> __device__ __forceinline__ double tw_sin<double>(int m) { return c_tws64[m]; }
 template <> __device__ __forceinline__ float tw_cos<float>(int m) { return c_twc32[m]; }
 template <> __device__ __forceinline__ float tw_sin<float>(int m) { return c_tws32[m]; }
+template <typename T> __device__ __forceinline__ T tw_lam(int m);
+template <typename T> __device__ __forceinline__ T tw_mu(int m);
+template <typename T> __device__ __forceinline__ T tw_rho(int m);
+template <> __device__ __forceinline__ double tw_lam<double>(int m) { return c_twl64[m]; }
+template <> __device__ __forceinline__ double tw_mu<double>(int m) { return c_twm64[m]; }
+template <> __device__ __forceinline__ double tw_rho<double>(int m) { return c_twr64[m]; }
+template <> __device__ __forceinline__ float tw_lam<float>(int m) { return c_twl32[m]; }
+template <> __device__ __forceinline__ float tw_mu<float>(int m) { return c_twm32[m]; }
+template <> __device__ __forceinline__ float tw_rho<float>(int m) { return c_twr32[m]; }
+
+// x i^e (e taken mod 4): a renaming with sign changes, no arithmetic.
+template <typename T>
+__device__ __forceinline__ void qturn(int e, T xr, T xi, T& yr, T& yi) {
+  e &= 3;
+  if (e == 0) {
+    yr = xr; yi = xi;
+  } else if (e == 1) {
+    yr = -xi; yi = xr;
+  } else if (e == 2) {
+    yr = -xr; yi = -xi;
+  } else {
+    yr = xi; yi = -xr;
+  }
+}
+
+// exp(SIGN 2 pi i m / 192) x = lam i^e u with u = x (1 + i mu): returns u already turned
+// by i^e and lam (1 for quarter turns, where u is x turned).  m is a compile-time constant
+// after unrolling, so the branches fold.
+template <int SIGN, typename T>
+__device__ __forceinline__ T tw_factor(int m, T xr, T xi, T& ur, T& ui) {
+  m %= kTw;
+  constexpr int Q = kTw / 4;
+  if (m % Q == 0) {
+    qturn<T>(SIGN * (m / Q), xr, xi, ur, ui);
+    return T(1);
+  }
+  const int r = m % (kTw / 2);
+  const bool cos_form = (r <= kTw / 8) || (r >= 3 * kTw / 8);
+  // cos form: w = cos (1 + i SIGN tan); sin form: w = (SIGN i) sin (1 - i SIGN cot)
+  const T mu = (cos_form ? T(SIGN) : T(-SIGN)) * tw_mu<T>(m);
+  const T vr = xr - mu * xi, vi = xi + mu * xr;
+  qturn<T>(cos_form ? 0 : SIGN, vr, vi, ur, ui);
+  return tw_lam<T>(m);
+}
 
 // Bit-reversal permutation of 0..N-1 as a compile-time table, so that the register
 // arrays below are only ever indexed by constants (otherwise they are placed in local
@@ -86,21 +146,45 @@ __device__ __forceinline__ void fft_stages(T (&xr)[N], T (&xi)[N]) {
 #pragma unroll
         for (int k = 0; k < SPAN; ++k) {
           const int i0 = s + k, i1 = i0 + SPAN, i2 = i1 + SPAN, i3 = i2 + SPAN;
-          T b1r, b1i, b2r, b2i, b3r, b3i;
-          twiddle<SIGN>(2 * k * stride, xr[i1], xi[i1], b1r, b1i);
-          twiddle<SIGN>(k * stride, xr[i2], xi[i2], b2r, b2i);
-          twiddle<SIGN>(3 * k * stride, xr[i3], xi[i3], b3r, b3i);
-          const T t0r = xr[i0] + b1r, t0i = xi[i0] + b1i;
-          const T t1r = xr[i0] - b1r, t1i = xi[i0] - b1i;
-          const T t2r = b2r + b3r, t2i = b2i + b3i;
-          const T t3r = b2r - b3r, t3i = b2i - b3i;
-          // (SIGN i) t3
-          const T u3r = (SIGN > 0) ? -t3i : t3i;
-          const T u3i = (SIGN > 0) ? t3r : -t3r;
-          xr[i0] = t0r + t2r; xi[i0] = t0i + t2i;
-          xr[i2] = t0r - t2r; xi[i2] = t0i - t2i;
-          xr[i1] = t1r + u3r; xi[i1] = t1i + u3i;
-          xr[i3] = t1r - u3r; xi[i3] = t1i - u3i;
+          const int mB = (k * stride) % kTw;  // w; w^2 at 2 mB, w^3 at 3 mB
+          // t0, t1 = x0 +- w^2 x1 with w^2 x1 = lamA u1
+          T u1r, u1i;
+          const T lamA = tw_factor<SIGN>(2 * mB, xr[i1], xi[i1], u1r, u1i);
+          T t0r, t0i, t1r, t1i;
+          if ((2 * mB) % (kTw / 4) == 0) {
+            t0r = xr[i0] + u1r; t0i = xi[i0] + u1i;
+            t1r = xr[i0] - u1r; t1i = xi[i0] - u1i;
+          } else {
+            t0r = xr[i0] + lamA * u1r; t0i = xi[i0] + lamA * u1i;
+            t1r = xr[i0] - lamA * u1r; t1i = xi[i0] - lamA * u1i;
+          }
+          // t2, t3 = w x2 +- w^3 x3 = lamB (u2 +- rho u3), rho = lamC / lamB; then
+          // y0, y2 = t0 +- t2 and y1, y3 = t1 +- (SIGN i) t3
+          T u2r, u2i, u3r, u3i;
+          const T lamB = tw_factor<SIGN>(mB, xr[i2], xi[i2], u2r, u2i);
+          tw_factor<SIGN>(3 * mB, xr[i3], xi[i3], u3r, u3i);
+          T pr, pi_, mr, mi;  // u2 + rho u3, u2 - rho u3
+          if (mB % (kTw / 4) == 0) {  // then 3 mB is a quarter turn as well: no factors
+            pr = u2r + u3r; pi_ = u2i + u3i;
+            mr = u2r - u3r; mi = u2i - u3i;
+          } else {
+            const T rho = tw_rho<T>(mB);
+            pr = u2r + rho * u3r; pi_ = u2i + rho * u3i;
+            mr = u2r - rho * u3r; mi = u2i - rho * u3i;
+          }
+          T qr, qi;  // (SIGN i) (u2 - rho u3)
+          qturn<T>(SIGN > 0 ? 1 : 3, mr, mi, qr, qi);
+          if (mB % (kTw / 4) == 0) {
+            xr[i0] = t0r + pr; xi[i0] = t0i + pi_;
+            xr[i2] = t0r - pr; xi[i2] = t0i - pi_;
+            xr[i1] = t1r + qr; xi[i1] = t1i + qi;
+            xr[i3] = t1r - qr; xi[i3] = t1i - qi;
+          } else {
+            xr[i0] = t0r + lamB * pr; xi[i0] = t0i + lamB * pi_;
+            xr[i2] = t0r - lamB * pr; xi[i2] = t0i - lamB * pi_;
+            xr[i1] = t1r + lamB * qr; xi[i1] = t1i + lamB * qi;
+            xr[i3] = t1r - lamB * qr; xi[i3] = t1i - lamB * qi;
+          }
         }
       }
       fft_stages<N, SIGN, 4 * SPAN>(xr, xi);

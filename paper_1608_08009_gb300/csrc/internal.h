@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/boltz.h"
+#include "twiddles.h"
 
 namespace boltz {
 
@@ -147,7 +148,7 @@ boltz_status dispatch_3d_large(const boltz_grid_s* g, const CollideArgs& a, int6
 boltz_status dispatch_2d(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st, int prec,
                          int f_is_fp64);
 #define BOLTZ_DECLARE_UNIT(TAG)                                                                                    \
-  cudaError_t unit_upload_twiddles_##TAG(const double* tc, const double* ts, const float* fc, const float* fs); \
+  cudaError_t unit_upload_twiddles_##TAG(const TwiddleTables& t);                                                 \
   cudaError_t unit_read_clear_status_##TAG(unsigned* value);
 BOLTZ_DECLARE_UNIT(f32)
 BOLTZ_DECLARE_UNIT(f64)
