@@ -60,6 +60,17 @@ constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusBadIndex = 4u;
 constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on an mbarrier gave up
 
+// Tensor memory budget.  tcgen05.alloc waits while the SM lacks a free, aligned block of
+// the requested columns, and a CTA that waits there while cluster peers on other SMs wait
+// for it (at a cluster barrier, holding their own columns) could close a cycle with the
+// CTAs of another kernel running on another stream.  So no allocation may ever wait:
+// every kernel that shares its SM takes exactly kTmemShare columns (one size, so the 512
+// columns never fragment) and enough shared memory that at most 8 such CTAs fit on an SM
+// (8 x 64 = 512 columns); a kernel that needs more columns takes enough shared memory
+// that no such CTA fits beside it.  tmem_launch_smem (host side, below) sizes both from
+// the device's own shared-memory attributes.
+constexpr int kTmemShare = 64;
+
 // Tensor-core transform modes of the float32 path (0: register FFT).
 constexpr int kTcNone = 0, kTcTF32 = 1, kTc3xBF16 = 2, kTc3xTF32 = 3;
 
@@ -92,8 +103,7 @@ struct CollideCfg {
   // (N = 16, 32: the pencil's real and imaginary halves are whole 16-column chunks)
   static constexpr bool kTmemSpec = kF32 && TC == kTcNone && N % 16 == 0;
   static constexpr int TMEM_NEED = ((THREADS / 32 + 3) / 4) * 2 * N;
-  static constexpr int TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128
-                                   : TMEM_NEED <= 256 ? 256 : 512;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
   // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
   // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
@@ -126,7 +136,11 @@ struct CollideCfg {
   static constexpr bool kAsyncScatter = kQuad && C > 1;
   static constexpr uint32_t SCATTER_BYTES = (uint32_t)NP * N * N * 2 * sizeof(T);  // received per term
   static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 24;
+  // TMEM columns held: the spectrum pencils, or the tensor-core accumulator (2N <= 64)
+  static constexpr int TC_TMEM_COLS = kTmemShare;
+  static constexpr int TMEM_HELD = kTmemSpec ? TMEM_COLS : (TC != kTcNone) ? TC_TMEM_COLS : 0;
   static_assert(TC == kTcNone || (kF32 && THREADS == 128), "tensor-core transforms: float32, 128 pencils per CTA");
+  static_assert(TC == kTcNone || 2 * N <= TC_TMEM_COLS, "tensor-core accumulator fits its columns");
   static_assert(THREADS % 32 == 0, "whole warps");
   static_assert(NP % VEC == 0, "whole chunks");
   static_assert(OFF_XB % 16 == 0 && (XB * sizeof(T2)) % 16 == 0, "16-byte aligned buffers");
@@ -157,6 +171,20 @@ __device__ __forceinline__ void cluster_barrier_war() {
   } else {
     __syncthreads();
   }
+}
+
+// The two halves of cluster_barrier_war (C > 1), for a caller with work that touches
+// neither side of the hazard between them: the arrive right after the last read, the
+// wait right before the first store into a peer.
+template <int C>
+__device__ __forceinline__ void cluster_arrive_war() {
+  static_assert(C > 1, "cluster only");
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+template <int C>
+__device__ __forceinline__ void cluster_wait_war() {
+  static_assert(C > 1, "cluster only");
+  asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
 }
 
 template <int C, typename P>
@@ -569,7 +597,7 @@ collide_kernel(const CollideArgs args) {
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TCB + 8);
     if ((threadIdx.x >> 5) == 0) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                   "r"(2 * N));
+                   "r"(Cfg::TC_TMEM_COLS));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
@@ -702,7 +730,15 @@ collide_kernel(const CollideArgs args) {
   if constexpr (kAsync) {
     if (threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
   }
-  if constexpr (Cfg::NXB == 1) cluster_barrier<C>();  // single buffer: peers done reading it
+  // Single buffer: the peers must be done reading this CTA's x-planes before the first
+  // scatter.  In a cluster the barrier is split: this arrive, and the wait inside the
+  // first kx pass just before its stores, so the transform runs meanwhile.
+  constexpr bool kSplitWar = (Cfg::NXB == 1) && (C > 1);
+  if constexpr (kSplitWar) {
+    cluster_arrive_war<C>();
+  } else if constexpr (Cfg::NXB == 1) {
+    cluster_barrier<C>();
+  }
 
   // ---- angular loop: one complex inverse transform per separated term --------------
   T acc[N];
@@ -736,6 +772,7 @@ collide_kernel(const CollideArgs args) {
       im[kx] = ab.x * c.y + ab.y * c.x;
     }
     inverse_1d();
+    if constexpr (kSplitWar) cluster_wait_war<C>();  // every owner has read its buffer
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
       T2* dst = XB + Cfg::elem(c * VEC, ky_own, kzt);
@@ -832,8 +869,16 @@ collide_kernel(const CollideArgs args) {
         if constexpr (kAsync) {
           if (threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
         }
-        cluster_barrier_war<C>();  // single buffer: owners done before the next scatter
+        // single buffer: owners done before the next scatter (its wait is in pass_kx)
+        if constexpr (kSplitWar) {
+          cluster_arrive_war<C>();
+        } else {
+          cluster_barrier_war<C>();
+        }
       }
+    }
+    if constexpr (kSplitWar) {
+      if (nt == 0) cluster_wait_war<C>();  // a group without terms: close the first arrive
     }
   }
 
@@ -849,7 +894,7 @@ collide_kernel(const CollideArgs args) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(2 * N));
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(Cfg::TC_TMEM_COLS));
   }
   if constexpr (kSplit) {
     // Partial gain (and the loss multiplier) of this group, then the last-arrival count
@@ -952,8 +997,7 @@ struct LargeCfg {
   // spectrum pencils in TMEM: warp w uses lanes 32 (w % 4) .. + 31 and the column group
   // w / 4 of 2N columns (N real parts, then N imaginary parts)
   static constexpr int TMEM_NEED = ((WARPS + 3) / 4) * 2 * N;
-  static constexpr int TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128
-                                   : TMEM_NEED <= 256 ? 256 : 512;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(TMEM_NEED <= 512, "spectrum slab fits TMEM");
   static_assert((2 * N) % 16 == 0, "whole 16-column TMEM chunks");
   static_assert(THREADS % 32 == 0 && NP % VEC == 0, "whole warps and chunks");
@@ -1450,6 +1494,32 @@ static inline boltz_status cuda_fail(cudaError_t e, const char* what) {
   return BOLTZ_ECUDA;
 }
 
+// Dynamic shared memory to launch a kernel with that holds `held` TMEM columns per CTA
+// (0: none; kTmemShare: shares the SM; more: must not share it with a TMEM holder), given
+// the `smem` bytes it uses.  With P bytes of shared memory per SM and r bytes kept by the
+// hardware per CTA, a sharing CTA takes at least P/9 - r + 1 bytes, so nine never fit; a
+// CTA holding more takes enough that not even one sharing CTA fits beside it.
+static inline boltz_status tmem_launch_smem(int held, size_t smem, int dev, size_t* out) {
+  *out = smem;
+  if (held == 0) return BOLTZ_OK;
+  int per_sm = 0, reserved = 0, optin = 0;
+  cudaError_t e;
+  if ((e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return cuda_fail(e, "shared memory attributes");
+  const size_t P = (size_t)per_sm, r = (size_t)reserved;
+  const size_t share = P / 9 + 1 - (r < P / 9 + 1 ? r : P / 9);
+  size_t need = share;
+  if (held > kTmemShare) need = P + 1 - share - 2 * r;  // (need + r) + (share + r) > P
+  if (need > *out) *out = need;
+  if (*out > (size_t)optin) {
+    set_error("shared memory reservation for tensor memory exceeds the per-block limit");
+    return BOLTZ_EUNSUPPORTED;
+  }
+  return BOLTZ_OK;
+}
+
 template <typename T, typename TIO, int N, int C, int TC = kTcNone>
 static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStream_t st) {
   using Cfg = CollideCfg<T, N, C, TC>;
@@ -1467,8 +1537,11 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const unsigned long long bit = 1ull << (dev & 63);
+  size_t smem = Cfg::SMEM;
+  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_HELD, Cfg::SMEM, dev, &smem);
+  if (ss != BOLTZ_OK) return ss;
   if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     if (C > 1) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1476,7 +1549,7 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
       cudaLaunchConfig_t q = {};
       q.gridDim = dim3(C, 1, 1);
       q.blockDim = dim3(Cfg::THREADS, 1, 1);
-      q.dynamicSmemBytes = Cfg::SMEM;
+      q.dynamicSmemBytes = smem;
       cudaLaunchAttribute qa[1];
       qa[0].id = cudaLaunchAttributeClusterDimension;
       qa[0].val.clusterDim.x = C;
@@ -1500,7 +1573,7 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
   cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
-  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1524,20 +1597,23 @@ static boltz_status launch_large_impl(const CollideArgs& a, int64_t n_cells, cud
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const unsigned long long bit = 1ull << (dev & 63);
+  size_t smem = Cfg::SMEM;
+  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_COLS, Cfg::SMEM, dev, &smem);
+  if (ss != BOLTZ_OK) return ss;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM)) !=
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess ||
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
       return cuda_fail(e, "cudaFuncSetAttribute");
     cudaLaunchConfig_t q = {};
     q.gridDim = dim3(C, 1, 1);
     q.blockDim = dim3(Cfg::THREADS, 1, 1);
-    q.dynamicSmemBytes = Cfg::SMEM;
+    q.dynamicSmemBytes = smem;
     q.attrs = attr;
     q.numAttrs = 1;
     int clusters = 0;
@@ -1555,7 +1631,7 @@ static boltz_status launch_large_impl(const CollideArgs& a, int64_t n_cells, cud
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_cells * a.groups * C), 1, 1);
   cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
-  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
