@@ -91,7 +91,7 @@ TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-cor
 # number of cells): profiles/collide_fp32_n32_2048cells.md and
 # profiles/collide_fp64_n32_512cells.md.  Must be re-taken (or set to None) whenever the
 # kernel changes.
-NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (286.921984e6 + 215.740672e6) / 2048, "fp64": None}
+NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (286.921984e6 + 215.740672e6) / 2048, "fp64": (172.5312e6 + 94.536704e6) / 512}
 
 
 def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
