@@ -601,13 +601,14 @@ def run_ours(args, wl):
     # downloads the result, copies pipelined with the compute chunk by chunk
     out_host = torch.empty_like(host).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
-    B.boltz_relax_host(batch, host, out_host, wl["dt"], 1, rk, 0, stream)  # staging set up outside the timing
+    hc = args.host_chunk_cells
+    B.boltz_relax_host(batch, host, out_host, wl["dt"], 1, rk, hc, stream)  # staging set up outside the timing
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        B.boltz_relax_host(batch, host, out_host, wl["dt"], 1, rk, 0, stream)
+        B.boltz_relax_host(batch, host, out_host, wl["dt"], 1, rk, hc, stream)
     e1.record(stream)
     barrier()
     B.boltz_stream_status(stream)
@@ -730,6 +731,8 @@ def main():
     ap.add_argument("--cells", type=int, default=0, help="override cells per GPU")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--host-chunk-cells", type=int, default=0,
+                    help="chunk size of the end-to-end boltz_relax_host run (0: the library's default schedule)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the float64 comparison of the batch")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving-load window (0: skip)")

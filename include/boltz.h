@@ -189,10 +189,12 @@ boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, double dt, int s
  * of boltz_relax).  f_in, f_out: host arrays of n_cells * N^3 elements (float32 or
  * float64 per f_is_fp64), owned by the caller; they may be the same array.  Page-locked
  * memory (cudaHostAlloc / cudaHostRegister) lets the copies overlap the compute; pageable
- * memory is accepted and serialises.  The batch runs in chunks of chunk_cells cells
- * (0: about an eighth of the batch, at least 512 cells, at most 1 GiB of f): the upload
- * of a chunk, the collision steps of the previous one and the download of the one
- * before run concurrently on two library streams and `stream`.  Returns once the work
+ * memory is accepted and serialises.  The batch runs in chunks (boltz_host_chunks gives
+ * them): chunk_cells > 0 gives equal chunks of that many cells; 0 gives the default, small
+ * chunks at both ends growing by 3/2 towards an eighth of the batch in the middle, so
+ * only a small first upload and a small last download stay exposed.  The upload of a
+ * chunk, the collision steps of the previous one and the download of the one before run
+ * concurrently on two library streams and `stream`.  Returns once the work
  * is enqueued; `stream` is ordered after the last download, so synchronise it (or call
  * boltz_stream_status) before reading f_out or reusing f_in.  The result equals
  * boltz_relax on the same cells bit for bit.  Staging buffers (three chunks, a Heun
@@ -200,6 +202,18 @@ boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, double dt, int s
  * on one grid must not overlap.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
 boltz_status boltz_relax_host(const boltz_batch* b, const void* f_in, void* f_out, double dt, int steps,
                               int rk_order, int64_t chunk_cells, void* stream);
+
+/* The chunks boltz_relax_host runs a batch in, for n_cells cells of cell_bytes bytes of f
+ * each (N^3 or N^2 values of 4 or 8 bytes) and its chunk_cells argument.  chunk_cells > 0:
+ * equal chunks of that many cells, the last one shorter.  0: a ramp of chunks from 32 MiB
+ * of f growing by 3/2 up to the middle size (an eighth of the batch, at least 64 MiB, at
+ * most 1 GiB of f), equal middle chunks, and the same ramp reversed, when the batch holds
+ * both ramps and one middle chunk; smaller batches get about eight equal chunks of at
+ * least 64 MiB (or the whole batch).  Host only, no device work.  Writes the first
+ * min(count, cap) chunk sizes to sizes (host array owned by the caller) and returns the
+ * number of chunks, or -1 on invalid arguments (n_cells, chunk_cells or cap negative,
+ * cell_bytes not positive, sizes null with cap > 0). */
+int64_t boltz_host_chunks(int64_t n_cells, int64_t cell_bytes, int64_t chunk_cells, int64_t* sizes, int64_t cap);
 
 /* ---- Ragged batches ------------------------------------------------------------------
  * A plan advances several groups of cells, each group on its own grid (any mix of N_v,

@@ -37,7 +37,7 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
             "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
             "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
-            "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint")
+            "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_host_chunks")
 
 
 class BoltzError(RuntimeError):
@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.boltz_moments.argtypes = [P(boltz_batch), vp, vp, vp]
         L.boltz_relax_noalloc.argtypes = [P(boltz_batch), vp, f64, i32, vp]
         L.boltz_relax_host.argtypes = [P(boltz_batch), vp, vp, f64, i32, i32, i64, vp]
+        L.boltz_host_chunks.argtypes = [i64, i64, i64, P(i64), i64]
+        L.boltz_host_chunks.restype = i64
         L.boltz_plan_create.argtypes = [P(boltz_group), i32, f64, i32, i32, i32, vp, P(vp)]
         L.boltz_plan_run.argtypes = [vp, vp]
         L.boltz_plan_group_info.argtypes = [vp, i32, P(i32), P(i32), P(f64)]
@@ -181,6 +183,16 @@ def boltz_relax_host(batch: boltz_batch, f_in, f_out, dt: float, steps: int, rk_
     Enqueued only: synchronise `stream` before reading f_out."""
     _check(lib().boltz_relax_host(ctypes.byref(batch), _ptr(f_in), _ptr(f_out), dt, steps, rk_order, chunk_cells,
                                   _stream(stream)))
+
+
+def boltz_host_chunks(n_cells: int, cell_bytes: int, chunk_cells: int = 0) -> list:
+    """The chunk sizes boltz_relax_host uses for this batch (host only)."""
+    n = lib().boltz_host_chunks(n_cells, cell_bytes, chunk_cells, None, 0)
+    if n < 0:
+        raise BoltzError(BOLTZ_EINVAL, lib().boltz_last_error().decode())
+    out = (ctypes.c_int64 * max(1, n))()
+    lib().boltz_host_chunks(n_cells, cell_bytes, chunk_cells, out, n)
+    return list(out[:n])
 
 
 def boltz_collide_indexed(batch: boltz_batch, f, Q, cell_idx, pool_cells: int, stream=None) -> None:

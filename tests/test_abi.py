@@ -65,3 +65,31 @@ def test_argument_errors_without_device(libboltz):
     assert "L must be" in B.boltz_last_error() or len(B.boltz_last_error()) > 0
     assert L.boltz_destroy_grid(None) == B.BOLTZ_OK
     assert L.boltz_grid_info(None, None, None, None, None, None, None) == B.BOLTZ_EINVAL
+
+
+def test_host_chunk_schedule(libboltz):
+    """boltz_relax_host's chunks: they tile the batch, stay within 1 GiB of f, and the
+    default ramps (32 MiB first and last chunks, growth 3/2) hold for large batches."""
+    cb = 32 ** 3 * 4  # one 32^3 float32 cell
+    c = B.boltz_host_chunks(32768, cb)
+    assert sum(c) == 32768 and min(c) > 0
+    assert c[0] == (32 << 20) // cb and c[-1] == c[0]
+    # ramp up by 3/2 until the middle size, about an eighth of the batch
+    up = [c[0]]
+    while c[len(up)] > up[-1] and c[len(up)] == up[-1] + up[-1] // 2:
+        up.append(c[len(up)])
+    assert len(up) >= 3
+    middle = c[len(up):len(c) - len(up)]
+    assert max(middle) - min(middle) <= 1 and abs(max(middle) - 32768 // 8) <= 32768 // 64
+    assert c[len(c) - len(up):] == up[::-1]
+    # explicit chunk size: equal chunks, last one shorter
+    assert B.boltz_host_chunks(1000, cb, 300) == [300, 300, 300, 100]
+    # small batch: one chunk; large cells are capped at 1 GiB per chunk
+    assert B.boltz_host_chunks(100, cb) == [100]
+    big = 64 ** 3 * 8
+    c = B.boltz_host_chunks(5000, big)
+    assert sum(c) == 5000 and max(c) * big <= (1 << 30)
+    assert B.boltz_host_chunks(0, cb) == []
+    with pytest.raises(B.BoltzError):
+        B.boltz_host_chunks(10, 0)
+    assert libboltz.boltz_host_chunks(-1, cb, 0, None, 0) == -1

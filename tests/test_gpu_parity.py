@@ -337,6 +337,26 @@ def test_relax_host_equals_device_relax(rk):
             assert torch.equal(inplace, ref)
 
 
+def test_relax_host_default_ramp():
+    """The default schedule of boltz_relax_host on a batch large enough for its ramps
+    (16384 cells of 16^3 float32: chunks from 2048 cells up to 4096 and back) gives
+    boltz_relax's result bit for bit."""
+    N, L, M, cells = 16, 6.0, 8, 16384
+    chunks = B.boltz_host_chunks(cells, N ** 3 * 4)
+    assert len(chunks) > 3 and chunks[0] < max(chunks) and chunks[-1] == chunks[0]
+    f = W.two_maxwellians(cells, N, L, seed=73)
+    with B.Grid(N, L, 1.0, M) as g:
+        batch = g.batch(cells, B.BOLTZ_FP32_FFT, False)
+        ref = torch.from_numpy(f).to(device="cuda", dtype=torch.float32)
+        B.boltz_relax(batch, ref, 0.004, 1, 1)
+        B.boltz_stream_status()
+        src = torch.from_numpy(f).to(torch.float32).pin_memory()
+        out = torch.empty_like(src).pin_memory()
+        B.boltz_relax_host(batch, src, out, 0.004, 1, 1)
+        B.boltz_stream_status()
+        assert torch.equal(out, ref.cpu())
+
+
 @pytest.mark.parametrize("N,L,M,groups", [(16, 6.0, 16, 2), (16, 6.0, 16, 5), (16, 6.0, 16, 16), (32, 8.0, 64, 8),
                                           (24, 7.0, 20, 3), (8, 4.0, 8, 8)])
 def test_term_groups_parity(N, L, M, groups):
