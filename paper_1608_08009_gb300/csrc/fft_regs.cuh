@@ -108,7 +108,8 @@ struct BitReverse {
 };
 
 // Complex multiply of (br, bi) by the twiddle exp(SIGN 2 pi i m / 192), m a compile-time
-// constant after unrolling (multiples of a quarter turn need no multiplication).
+// constant after unrolling (multiples of a quarter turn need no multiplication); used by
+// the radix-2 and radix-3 combinations.
 template <int SIGN, typename T>
 __device__ __forceinline__ void twiddle(int m, T br, T bi, T& tr, T& ti) {
   m %= kTw;
@@ -131,10 +132,11 @@ __device__ __forceinline__ void twiddle(int m, T br, T bi, T& tr, T& ti) {
 }
 
 // Decimation-in-time stages on bit-reversed input.  SPAN is the length of the
-// sub-transforms already formed; a radix-4 stage merges four of them (span 4 SPAN,
-// three twiddle multiplications per four points, the inner factor SIGN i is a swap), a
-// radix-2 stage two of them.  Spans are template parameters so every loop has
-// compile-time bounds and unrolls fully: register indices are all constants.
+// sub-transforms already formed; a radix-4 stage merges four of them (span 4 SPAN; the
+// twiddles w^2, w, w^3 of the four points in factored form, the inner factor SIGN i a
+// swap), a radix-2 stage two of them (plain complex multiply).  Spans are template
+// parameters so every loop has compile-time bounds and unrolls fully: register indices
+// are all constants.
 template <int N, int SIGN, int SPAN, typename T>
 __device__ __forceinline__ void fft_stages(T (&xr)[N], T (&xi)[N]) {
   if constexpr (SPAN < N) {
