@@ -233,6 +233,46 @@ def test_full_size_fp64_sampled():
         assert rel_l2(Q[sample].cpu().numpy(), Qref) <= 1e-12
 
 
+def test_full_size_mixed_sampled():
+    """32768 cells x 32^3, M = 64, float32 storage and transforms: the batch and launch the
+    throughput benchmark times (seed 20163).  Sampled cells of Q against the oracle (on the
+    float32-rounded input); on every cell the conserved moments of the projected Q vanish
+    to the float32 rounding of its values; one relax step equals f + dt Q cell for cell
+    within the float32 rounding of the result."""
+    n_cells, N, L, M, seed, dt = 32768, 32, 8.0, 64, 20163, 0.0025
+    with B.Grid(N, L, 1.0, M) as g:
+        batch = g.batch(n_cells, B.BOLTZ_FP32_FFT, False)
+        f = torch.empty(n_cells, N, N, N, dtype=torch.float32)
+        for c0 in range(0, n_cells, 1024):
+            f[c0:c0 + 1024] = torch.from_numpy(W.two_maxwellians(n_cells, N, L, seed, cells=range(c0, c0 + 1024)))
+        fd = f.cuda()
+        Q = torch.empty_like(fd)
+        B.boltz_collide(batch, fd, Q)
+        B.boltz_stream_status()
+        # conservation on every cell: mass and energy of Q against those of |Q|
+        U = torch.empty(n_cells, 5, dtype=torch.float64, device="cuda")
+        UA = torch.empty(n_cells, 5, dtype=torch.float64, device="cuda")
+        B.boltz_moments(batch, Q, U)
+        B.boltz_moments(batch, Q.abs(), UA)
+        assert (U[:, 0].abs() / UA[:, 0]).max().item() < 8 * EPS32
+        assert (U[:, 4].abs() / UA[:, 4]).max().item() < 8 * EPS32
+        # sampled cells against the oracle
+        sample = [0, 1, 16383, 32767]
+        f_s = f[sample].double().numpy()
+        og = oracle_grid(N, L, M)
+        Qref = O.collide(f_s, og)
+        tol = fp32_tol(f_s, og) + EPS32
+        assert rel_l2(Q[sample].double().cpu().numpy(), Qref) <= tol
+        # one Euler step of the relax launch the benchmark times: f + dt Q with the
+        # projection targets of f itself, stored as float32
+        B.boltz_relax(batch, fd, dt, 1, 1)
+        B.boltz_stream_status()
+        step = fd[sample].double().cpu() - f[sample].double()
+        expect = torch.from_numpy(dt * Q[sample].double().cpu().numpy())
+        err = (step - expect).abs().max().item()
+        assert err <= 4 * EPS32 * f[sample].abs().max().item() + tol * expect.abs().max().item()
+
+
 def test_indexed_cells_match_contiguous_batch():
     N, L, M, pool = 16, 6.0, 16, 9
     f = W.two_maxwellians(pool, N, L, seed=61)
