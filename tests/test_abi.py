@@ -93,3 +93,27 @@ def test_host_chunk_schedule(libboltz):
     with pytest.raises(B.BoltzError):
         B.boltz_host_chunks(10, 0)
     assert libboltz.boltz_host_chunks(-1, cb, 0, None, 0) == -1
+
+
+def test_argument_errors_of_the_other_entry_points(libboltz):
+    """Every entry point rejects missing handles and arguments with a status before any
+    CUDA call (no device needed); destroying a null grid is a no-op."""
+    L = libboltz
+    h = ctypes.c_void_p()
+    assert L.boltz_create_grid2d(12, 8.0, 8, None, ctypes.byref(h)) == B.BOLTZ_EUNSUPPORTED
+    assert L.boltz_create_grid2d(32, -1.0, 8, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert L.boltz_create_grid2d(32, 8.0, 0, None, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert L.boltz_create_grid2d(32, 8.0, 8, None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_relax_host(None, None, None, 0.1, 1, 1, 0, None) == B.BOLTZ_EINVAL
+    assert L.boltz_relax_noalloc(None, None, 0.1, 1, None) == B.BOLTZ_EINVAL
+    assert L.boltz_collide_indexed(None, None, None, None, 0, None) == B.BOLTZ_EINVAL
+    assert L.boltz_relax_indexed(None, None, None, 0, 0.1, 1, None) == B.BOLTZ_EINVAL
+    assert L.boltz_plan_create(None, 0, 0.1, 1, 1, 0, None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_plan_run(None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_server_create(None, 0, 1, 0.1, 0, None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_server_submit(None, 0, None, None, 1, None) == B.BOLTZ_EINVAL
+    assert L.boltz_server_step(None, None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_server_poll(None, 0, None) == B.BOLTZ_EINVAL
+    assert L.boltz_grid_info(None, None, None, None, None, None, None) == B.BOLTZ_EINVAL
+    assert L.boltz_last_error()  # the message of the last failure
+    assert L.boltz_destroy_grid(None) == B.BOLTZ_OK
