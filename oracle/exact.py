@@ -122,6 +122,21 @@ def hs_collision_frequency(v, rho, u, T, C_gamma: float = 1.0):
     return 4.0 * math.pi * C_gamma * rho * math.sqrt(2.0 * T) * mean
 
 
+def vhs_collision_frequency(v, rho, u, T, gamma: float, C_gamma: float = 1.0):
+    """int int_{S^2} C |v - w|^gamma M(w) d omega dw = 4 pi C rho E|Z|^gamma, Z ~ N(v - u, T I).
+
+    The moments of the non-central chi distribution with three degrees of freedom:
+    E|Z|^g = (2T)^{g/2} Gamma((3 + g)/2) / Gamma(3/2) 1F1(-g/2; 3/2; -c^2),
+    c = |v - u| / sqrt(2T) (Kummer's function from scipy).  g = 0 gives 1, g = 1 the
+    erf form of hs_collision_frequency.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    c2 = np.sum((v - np.asarray(u)) ** 2, axis=-1) / (2.0 * T)
+    mean = ((2.0 * T) ** (0.5 * gamma) * special.gamma(0.5 * (3.0 + gamma)) / special.gamma(1.5)
+            * special.hyp1f1(-0.5 * gamma, 1.5, -c2))
+    return 4.0 * math.pi * C_gamma * rho * mean
+
+
 def _sphere_rule(nt: int, npp: int):
     """Gauss-Legendre in cos(theta) x trapezoid in varphi on S^2: nodes [P, 3], weights [P]."""
     ct, ut = np.polynomial.legendre.leggauss(nt)

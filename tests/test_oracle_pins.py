@@ -162,6 +162,28 @@ def test_loss_is_hard_sphere_collision_frequency(grid32):
     assert np.max(np.abs(Lo[sel] - nu[sel]) / nu[sel]) < 1e-5
 
 
+@pytest.mark.parametrize("gamma", [0.5, 0.0])
+def test_loss_is_vhs_collision_frequency(gamma):
+    """gamma != 1 through the rank-r radial expansion: for |q| <= R the loss multiplier
+    equals the VHS collision frequency 4 pi C int |v - w|^gamma f(w) dw (closed form for a
+    Maxwellian; gamma = 0 is the constant 4 pi C rho of Maxwell molecules).  A wrong
+    exponent misses by 30 % or more."""
+    g = O.make_grid(32, 8.0, gamma=gamma, M=64, dirs_kind=2)
+    VX, VY, VZ = _mesh(g)
+    u = np.array([0.1, 0.0, -0.2])
+    M1 = E.maxwellian(VX, VY, VZ, 0.8, u, 0.9)
+    Lo = O.operator.inverse(g.D * O.operator.forward(M1, g), g).real
+    V = np.stack([VX, VY, VZ], axis=-1)
+    nu = E.vhs_collision_frequency(V, 0.8, u, 0.9, gamma)
+    sel = np.linalg.norm(V, axis=-1) < 1.5
+    assert np.max(np.abs(Lo[sel] - nu[sel]) / nu[sel]) < 1e-5
+    if gamma == 0.0:
+        assert np.allclose(nu, 4.0 * math.pi * 0.8, rtol=1e-14)
+    # the two closed forms agree at gamma = 1
+    assert np.allclose(E.vhs_collision_frequency(V, 0.8, u, 0.9, 1.0), E.hs_collision_frequency(V, 0.8, u, 0.9),
+                       rtol=1e-12)
+
+
 def test_direct_quadrature_of_boltzmann_integral(grid32):
     g = grid32
     gs = [(0.6, np.array([0.5, 0.3, -0.2]), 0.4), (0.4, np.array([-0.6, -0.2, 0.3]), 0.3)]
