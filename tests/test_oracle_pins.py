@@ -150,6 +150,23 @@ def test_maxwellian_is_equilibrium_spectrally():
     assert errs[2] < 1e-4
 
 
+@pytest.mark.parametrize("gamma", [0.5, 0.0])
+def test_maxwellian_is_equilibrium_rank_expansion(gamma):
+    """Q(M, M) = 0 (Eq. i6) through the rank-r radial expansion of Eq. Btilde for
+    gamma != 1: the gain equals M times the loss up to the resolution of the grid and the
+    radial quadrature.  (A factor common to alpha' cancels here; the collision-frequency
+    pin fixes it.)"""
+    errs = []
+    for N in (16, 24):
+        g = O.make_grid(N, 8.0, gamma=gamma, M=64, dirs_kind=2)
+        VX, VY, VZ = _mesh(g)
+        M1 = E.maxwellian(VX, VY, VZ, 1.3, np.array([0.2, -0.1, 0.05]), 1.0)
+        Qp, Lo = O.operator.gain_loss(M1, g)
+        errs.append(np.linalg.norm(Qp - M1 * Lo) / np.linalg.norm(Qp))
+    assert errs[0] > 10 * errs[1]
+    assert errs[1] < 1e-4
+
+
 def test_loss_is_hard_sphere_collision_frequency(grid32):
     g = grid32
     VX, VY, VZ = _mesh(g)
