@@ -1,7 +1,8 @@
 """Pins of the 2D Maxwell-molecule oracle (oracle/plane.py) against what the paper and the
 mathematics fix: the 2D BKW closed form (Sec. 5, Test 1.1), the error magnitudes the
 paper prints for it (Table test1, tests/golden/bkw2d_table_test1.json), the wrapped O(n^2)
-spectral sum, exact mass conservation and the projection."""
+spectral sum, exact mass conservation and the projection, the Maxwell-molecule collision
+frequency (the loss multiplier is the density) and the exact symmetries of the operator."""
 
 import json
 import math
@@ -92,3 +93,39 @@ def test_maxwellian_is_spectrally_close_to_equilibrium():
         Qp, Lo = P.gain_loss(M, g)
         errs.append(np.linalg.norm(Qp - M * Lo) / np.linalg.norm(Qp))
     assert errs[1] < 1e-5 and errs[1] < errs[0] / 10
+
+
+def test_loss_is_the_density_for_maxwell_molecules():
+    """With the kernel normalised so that the BKW closed form holds (B = 1/(2 pi) on the
+    unit circle, Btilde = 1/pi), the collision frequency of Maxwell molecules is
+    int f(w) dw int_{S^1} B d sigma = rho: the loss multiplier of the fast method is the
+    density wherever |v - w| <= R covers the support of f."""
+    for N, L, A in ((32, 9.0, 8), (32, 9.0, 32)):
+        g = P.make_plane_grid(N, L, A=A)
+        VX, VY = np.meshgrid(g.v, g.v, indexing="ij")
+        rho, T = 0.8, 1.0
+        f = rho / (2 * math.pi * T) * np.exp(-((VX - 0.2) ** 2 + (VY + 0.1) ** 2) / (2 * T))
+        _, Lo = P.gain_loss(f, g)
+        sel = np.hypot(VX, VY) < 2.0
+        assert np.max(np.abs(Lo[sel] - rho)) < 1e-6 * rho
+
+
+def test_symmetries_are_exact():
+    """Exact invariances of the periodised operator on the grid: circular shifts by whole
+    grid steps (Galilean invariance), Q[c f] = c^2 Q[f], the reflection v -> -v and, since
+    the angles pi p / A are invariant under a quarter turn for even A, the rotation by
+    90 degrees."""
+    N = 16
+    g = P.make_plane_grid(N, 6.0, A=8)
+    rng = np.random.default_rng(9)
+    f = P.bkw(g, 0.7) * (1.0 + 0.2 * rng.random((N, N)))
+    Q = P.collide(f, g, project=False)
+    scale = np.abs(Q).max()
+    shift = lambda a: np.roll(np.roll(a, 3, axis=0), -2, axis=1)
+    assert np.max(np.abs(P.collide(shift(f), g, project=False) - shift(Q))) < 1e-13 * scale
+    assert np.max(np.abs(P.collide(2.5 * f, g, project=False) - 6.25 * Q)) < 1e-13 * scale
+    idx = (-np.arange(N)) % N
+    reflect = lambda a: a[np.ix_(idx, idx)]
+    assert np.max(np.abs(P.collide(reflect(f), g, project=False) - reflect(Q))) < 1e-13 * scale
+    rotate = lambda a: a.T[idx, :]  # (i, j) -> (-j, i): (vx, vy) -> (-vy, vx)
+    assert np.max(np.abs(P.collide(rotate(f), g, project=False) - rotate(Q))) < 1e-13 * scale
