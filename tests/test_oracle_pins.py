@@ -277,6 +277,25 @@ def test_bilinearity_and_reflection():
     assert np.max(np.abs(Qr - ref(Q))) < 1e-13 * np.abs(Q).max()
 
 
+@pytest.mark.parametrize("kind", [0, 2])
+def test_quarter_turn_about_vz_is_exact(kind):
+    """The operator commutes with rotations of velocity space; on the grid, a quarter turn
+    about v_z maps grid points to grid points, and the product direction sets (azimuths
+    (q + 1/2) pi / A2 with A2 even) are mapped onto themselves (e and -e give the same
+    term), so the fast operator commutes with it exactly.  A quarter turn about v_x does
+    not preserve the direction set: there the difference is the quadrature error."""
+    N = 16
+    g = O.make_grid(N, 6.0, M=64, dirs_kind=kind)
+    f = W.two_maxwellians(1, N, 6.0, seed=11)[0]
+    Q = O.collide(f, g, project=False)
+    idx = (-np.arange(N)) % N
+    turn_z = lambda a: np.transpose(a, (1, 0, 2))[idx, :, :]  # (vx, vy, vz) -> (-vy, vx, vz)
+    assert np.max(np.abs(O.collide(turn_z(f), g, project=False) - turn_z(Q))) < 1e-12 * np.abs(Q).max()
+    turn_x = lambda a: np.transpose(a, (0, 2, 1))[:, idx, :]  # (vx, vy, vz) -> (vx, -vz, vy)
+    dx = np.max(np.abs(O.collide(turn_x(f), g, project=False) - turn_x(Q))) / np.abs(Q).max()
+    assert 1e-6 < dx < 3e-2
+
+
 def test_relax_conserves_and_heun_is_second_order():
     g = O.make_grid(16, 6.0, M=16, dirs_kind=0)
     f0 = W.two_maxwellians(1, 16, 6.0, seed=3)[0]
