@@ -47,9 +47,9 @@ typedef enum {
   BOLTZ_EINVAL = 1,        /* bad argument (null pointer, size, unsupported value)      */
   BOLTZ_ENOMEM = 2,        /* host or device allocation failed                          */
   BOLTZ_ECUDA = 3,         /* a CUDA runtime call failed (message in boltz_last_error)  */
-  BOLTZ_EUNSUPPORTED = 4,  /* valid request this build has no kernel for (e.g. N, prec)  */
+  BOLTZ_EUNSUPPORTED = 4,  /* valid request the library has no kernel for (e.g. N, prec) */
   BOLTZ_ENONFINITE = 5,    /* device status: a NaN or Inf was produced                  */
-  BOLTZ_ETIMEOUT = 6       /* device status: a bounded wait gave up (not used yet)      */
+  BOLTZ_ETIMEOUT = 6       /* device status: a bounded mbarrier wait in a kernel gave up  */
 } boltz_status;
 
 /* Arithmetic of the transforms and angular products (the hot loop).  Moments, the

@@ -44,7 +44,7 @@ boltz_status check_batch(const boltz_batch* b) {
     return BOLTZ_EINVAL;
   }
   if (!boltz::collide_supported_grid(b->grid, b->prec)) {
-    set_error("this precision has no kernel for this N in this build");
+    set_error("this precision has no kernel for this N in this library");
     return BOLTZ_EUNSUPPORTED;
   }
   return BOLTZ_OK;
@@ -91,7 +91,7 @@ boltz_status boltz_create_grid(int N_v, double L, double gamma, int M_dirs, cons
     return BOLTZ_EINVAL;
   }
   if (N_v != 8 && N_v != 16 && N_v != 24 && N_v != 32 && N_v != 48 && N_v != 64) {
-    set_error("N_v must be 8, 16, 24, 32, 48 or 64 in this build");
+    set_error("N_v must be 8, 16, 24, 32, 48 or 64 in this library");
     return (N_v > 0 && N_v % 2 == 0) ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
   }
   if (!(L > 0) || !std::isfinite(L)) {
@@ -181,7 +181,7 @@ boltz_status boltz_create_grid2d(int N_v, double L, int M_dirs, const boltz_grid
     return BOLTZ_EINVAL;
   }
   if (N_v != 8 && N_v != 16 && N_v != 32 && N_v != 64) {
-    set_error("2D grids: N_v must be 8, 16, 32 or 64 in this build");
+    set_error("2D grids: N_v must be 8, 16, 32 or 64 in this library");
     return (N_v > 0 && N_v % 2 == 0) ? BOLTZ_EUNSUPPORTED : BOLTZ_EINVAL;
   }
   if (!(L > 0) || !std::isfinite(L)) {

@@ -66,7 +66,7 @@ extern "C" boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, doubl
     return BOLTZ_EINVAL;
   }
   if (!boltz::collide_supported_grid(b->grid, b->prec)) {
-    boltz::set_error("this precision has no kernel for this N in this build");
+    boltz::set_error("this precision has no kernel for this N in this library");
     return BOLTZ_EUNSUPPORTED;
   }
   if (!(dt > 0) || !(dt < 1e300)) {
