@@ -25,8 +25,8 @@
  *              stream).  Every compute call is asynchronous on that stream.
  *  Errors.     Argument errors are returned synchronously and leave the stream
  *              untouched.  Conditions found on the device (non-finite results, cell
- *              indices outside their pool) are
- *              OR-ed into a device status word that boltz_stream_status() reads.  No call
+ *              indices outside their pool, a bounded wait that gave up) are OR-ed
+ *              into a device status word that boltz_stream_status() reads.  No call
  *              aborts, traps or waits without bound.  boltz_last_error() gives a
  *              thread-local message for the last failing call of the calling thread.
  *  Devices.    A grid is bound to the device that was current when it was created;
@@ -88,14 +88,15 @@ typedef struct {
   int term_groups;   /* split each cell's separated terms over this many thread-block
                         clusters (1 = default: one cluster per cell).  G > 1 lowers the
                         latency of batches too small to fill the GPU at the cost of G - 1
-                        extra forward transforms per cell and a second launch that sums
-                        the partial gains and runs the epilogue; it needs device scratch
-                        of (G + 1) N^3 values per cell (grown on demand, kept with the
-                        grid).  Clamped to [1, M_eff].  Results depend on G (rounding
+                        extra forward transforms per cell; the cluster that finishes a
+                        cell's last group (a per-cell arrival counter, no waiting) sums
+                        the partial gains in group order and runs the epilogue.  Needs
+                        device scratch of (G + 1) N^3 values per cell (grown on demand,
+                        kept with the grid).  Clamped to [1, M_eff].  Results depend on G (rounding
                         order of the gain sum) but not on the batch size.               */
   int cluster_size;  /* thread-block cluster size (CTAs per cell) of the float32 path;
-                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 8).  Also built:
-                        16: 2, 4; 24: 2, 6; 32: 4, 16.  Larger clusters give each CTA
+                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 8, 48: 8, 64: 16).  Also
+                        built: 16: 2, 4; 24: 2, 6; 32: 4, 16.  Larger clusters give each CTA
                         a thinner slab (fewer threads, more CTAs per SM).  The float64
                         path always uses its own size (8: 1, 16: 2, 24: 3, 32: 8).
                         Results agree across sizes up to the rounding of the moment sums
@@ -311,8 +312,10 @@ boltz_status boltz_server_destroy(boltz_server s);
 boltz_status boltz_moments(const boltz_batch* b, const void* f, double* U, void* stream);
 
 /* Synchronise `stream`, then read and clear the device status word of the current
- * device.  Returns BOLTZ_OK, BOLTZ_ENONFINITE, or BOLTZ_ECUDA if the stream itself
- * reported an error. */
+ * device.  Returns BOLTZ_ECUDA if the stream itself reported an error, else the first
+ * condition the word holds of: BOLTZ_ETIMEOUT (a bounded mbarrier wait gave up; that
+ * launch's results are invalid), BOLTZ_EINVAL (a cell index outside its pool; that cell
+ * was not written), BOLTZ_ENONFINITE (a NaN or Inf was produced); else BOLTZ_OK. */
 boltz_status boltz_stream_status(void* stream);
 
 /* Thread-local message of the last failing call of this thread ("" if none). */

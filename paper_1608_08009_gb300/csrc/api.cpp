@@ -438,7 +438,7 @@ boltz_status boltz_stream_status(void* stream) {
   boltz_status st = boltz::read_and_clear_status((cudaStream_t)stream, &v);
   if (st != BOLTZ_OK) return st;
   if (v & 8u) {
-    set_error("a bounded wait for the tensor cores gave up (results of that launch are invalid)");
+    set_error("a bounded mbarrier wait in a kernel gave up (results of that launch are invalid)");
     return BOLTZ_ETIMEOUT;
   }
   if (v & 4u) {
