@@ -91,12 +91,12 @@ def make_inputs(wl: dict, cells, total: int):
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 NOMINAL_FP64_TFLOPS = 1.25                            # GB300 FP64 (non-tensor), nominal
 TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-core rate ratio
-# DRAM bytes (read + write) per cell of one collide_kernel launch, from one ncu capture of
-# the current kernels on a smaller batch of the same workload (traffic grows with the
-# number of cells): profiles/collide_fp32_n32_2048cells.md and
-# profiles/collide_fp64_n32_512cells.md.  Must be re-taken (or set to None) whenever the
-# kernel changes.
-NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (286.921984e6 + 215.740672e6) / 2048, "fp64": (172.5312e6 + 94.536704e6) / 512}
+# DRAM bytes (read + write) per cell of one collide_kernel launch, taken from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as built, on 2048
+# cells (float32 path) and 512 cells (float64 path) of the same workload, divided by the
+# cells of that capture (traffic grows in proportion to the cells: one read of f and one
+# write of the result per cell).  None when the kernel has changed since the capture.
+NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": None, "fp64": None}
 
 
 def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
@@ -210,6 +210,25 @@ def cpu_oracle_rate_cores(wl: dict, budget_s: float, cores: int = 0):
     done = sum(r[1] for r in res)
     el = max(r[2] for r in res)
     return done / el, done, el, cores
+
+
+def cpu_model() -> str:
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096, first: int = 0, stride: int = 1):
@@ -511,6 +530,71 @@ def config_of(args, wl):
             "parallelism": f"cells sharded, {args.gpus} GPU(s)"}
 
 
+def run_targets(args, wl, grid, value, stream) -> dict:
+    """The clauses of the mixed-precision target beside the headline number, measured in
+    the same run (rank 0):
+
+    * moment drift on a float64 master state: the headline batch (all its cells) stored
+      in float64, 20 Euler steps of the same float32-transform kernel family; relative
+      drift of mass, momentum (scaled by sqrt(2 rho E)) and energy per cell, max over cells;
+    * the plain float64 form on its own configuration (4096 cells x 32^3, M = 64, float64
+      everywhere): cell-collisions/s, event-timed, and the headline's factor over it."""
+    import torch
+
+    from paper_1608_08009_gb300 import boltz as B
+
+    out = {}
+    cells = wl["cells"]
+    # ---- float64 master: same cells, f stored float64, float32 transforms --------------
+    f = torch.empty((cells,) + (wl["N"],) * 3, dtype=torch.float64, device="cuda")
+    for c0 in range(0, cells, 1024):
+        c1 = min(cells, c0 + 1024)
+        f[c0:c1] = torch.from_numpy(make_inputs(wl, range(c0, c1), cells)).cuda()
+    batch = grid.batch(cells, B.BOLTZ_FP32_FFT, True)
+    U0 = torch.empty(cells, 5, dtype=torch.float64, device="cuda")
+    B.boltz_moments(batch, f, U0, stream)
+    steps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.boltz_relax(batch, f, wl["dt"], steps, 1, stream)
+    e1.record(stream)
+    U1 = torch.empty_like(U0)
+    B.boltz_moments(batch, f, U1, stream)
+    B.boltz_stream_status(stream)
+    scale = U0.abs().clone()
+    scale[:, 1:4] = torch.sqrt(2.0 * U0[:, :1] * U0[:, 4:5]).expand(-1, 3)
+    drift = ((U1 - U0).abs() / scale).max(dim=0).values.cpu().tolist()
+    out["f64_master"] = {"cells": cells, "steps": steps, "moment_drift_rel": drift, "max_drift": max(drift),
+                         "value": cells * steps / (e0.elapsed_time(e1) / 1000.0), "unit": "cell-collisions/s",
+                         "storage": "f stored f64, transforms f32, moments/projection/update f64"}
+    del f, U0, U1
+    # ---- the plain float64 form on its configuration ----------------------------------
+    w64 = WORKLOADS["fp64_32"]
+    c64 = w64["cells"]
+    f = torch.empty((c64,) + (w64["N"],) * 3, dtype=torch.float64, device="cuda")
+    for c0 in range(0, c64, 1024):
+        c1 = min(c64, c0 + 1024)
+        f[c0:c1] = torch.from_numpy(make_inputs(w64, range(c0, c1), c64)).cuda()
+    b64 = grid.batch(c64, B.BOLTZ_FP64, True)
+    B.boltz_relax(b64, f, w64["dt"], 1, 1, stream)  # warm-up
+    torch.cuda.synchronize()
+    k = 3
+    e0.record(stream)
+    for _ in range(k):
+        B.boltz_relax(b64, f, w64["dt"], 1, 1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.boltz_stream_status(stream)
+    r64 = c64 * k / (e0.elapsed_time(e1) / 1000.0)
+    out["fp64_form"] = {"workload": "fp64_32", "cells": c64, "steps": k, "value": r64, "unit": "cell-collisions/s",
+                        "flops_frac_of_nominal_fp64": algorithmic_flops(w64["N"], w64["M"]) * r64 / 1e12
+                        / NOMINAL_FP64_TFLOPS}
+    out["factor_vs_fp64_form"] = value / r64
+    del f
+    return out
+
+
 def run_ours(args, wl):
     import torch
 
@@ -661,6 +745,13 @@ def run_ours(args, wl):
         err = ((Qx.double() - Q64).norm() / Q64.norm()).item()
         del Qx, f64, Q64
 
+    targets = None
+    if (rank == 0 and args.workload == "mixed32" and not args.no_accuracy and not args.no_targets
+            and wl["prec"] == "fp32_fft"):
+        targets = run_targets(args, wl, grid, value, stream)
+        targets["err_vs_fp64"] = err
+        targets["spec"] = {"err_vs_fp64_max": 1e-5, "moment_drift_max": 1e-10, "roofline_frac_min": 0.5}
+
     if rank == 0:
         peaks = measured_peaks()
         flops_cell = algorithmic_flops(N, grid.info["M_eff"], dim)
@@ -710,14 +801,21 @@ def run_ours(args, wl):
             "moment_drift_rel": drift,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }
+        if targets is not None:
+            targets["roofline_frac"] = achieved / peak
+            line["targets"] = targets
         if args.serve_seconds > 0 and ws == 1:
             line["serve"] = run_serving(args.serve_seconds, term_groups=args.serve_groups)
         if not args.no_cpu_baseline and ws == 1:
             r, ncell, el, cores = cpu_oracle_rate_cores(wl, budget_s=args.cpu_budget)
+            r1, n1, el1 = cpu_oracle_rate(wl, budget_s=min(10.0, args.cpu_budget))
             line["cpu_baseline"] = {"value": r, "unit": "cell-collisions/s", "cores": cores, "kind": "oracle",
                                     "sample": f"{ncell} cell-collisions of the same workload (cells strided over "
                                               f"{cores} spawned processes, one FP64 numpy oracle step each), "
-                                              f"{el:.1f} s"}
+                                              f"{el:.1f} s",
+                                    "cpu_model": cpu_model(), "hardware_threads": os.cpu_count(),
+                                    "one_core": {"value": r1, "unit": "cell-collisions/s", "cores": 1,
+                                                 "sample": f"{n1} cell-collisions in {el1:.1f} s, this process"}}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -740,6 +838,8 @@ def main():
                     help="chunk size of the end-to-end boltz_relax_host run (0: the library's default schedule)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the float64 comparison of the batch")
+    ap.add_argument("--no-targets", action="store_true",
+                    help="skip the float64-master drift and plain float64 form legs of the default workload")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving-load window (0: skip)")
     ap.add_argument("--serve-groups", type=str, default="",
                     help="term groups of the serving grids, e.g. 16:4,32:8 (default)")

@@ -170,18 +170,22 @@ boltz_status boltz_collide(const boltz_batch* b, const void* f, void* Q, void* s
 boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, int rk_order,
                          void* stream);
 
-/* Forward-Euler relaxation exactly as boltz_relax with rk_order 1, but allocating no
- * memory: the paper has no counterpart; this exists for callers that cannot let the
- * library call cudaMalloc / cudaFree (a framework whose caching allocator holds the
- * device memory, a stepping loop that must not stall on the device-wide synchronisation
- * a free implies, an embedding that forbids library-owned device memory).  The per-cell
- * moment targets live in a fixed array inside the library's device image, 65536 cells
- * * 5 doubles (2.5 MiB), held on every device that loads the library until process
- * exit.  n_cells above 65536 returns BOLTZ_EINVAL.  All calls on a device share that
- * array and it keeps the last call's contents; each call rewrites the targets of all
- * its cells before using them, but calls that overlap on the GPU race on the array, so
- * serialise them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it: make that first call before any stream capture.
+/* Forward-Euler relaxation as boltz_relax with rk_order 1, allocating no memory.  The
+ * paper has no counterpart; this exists for callers that cannot let the library call
+ * cudaMalloc / cudaFree (a framework whose caching allocator holds the device memory, a
+ * stepping loop that must not stall on the device-wide synchronisation a free implies,
+ * an embedding that forbids library-owned device memory).  The per-cell moment targets
+ * live in a fixed array inside the library's device image, 65536 cells * 5 doubles
+ * (2.5 MiB), held on every device that loads the library until process exit.
+ * n_cells above 65536 returns BOLTZ_EINVAL.  It runs boltz_relax's launches with one
+ * term group: on a grid with term_groups = 1 the result equals boltz_relax (rk_order 1)
+ * bit for bit; with term_groups > 1 it equals it up to the rounding of the gain sum.
+ * All calls on a device share the array and it keeps the last call's contents; each
+ * call's first launch rewrites the targets of all its cells before they are read, but
+ * calls that overlap on the GPU race on the array, so serialise them.  Each call made
+ * while its stream is not capturing looks the array's device address up
+ * (cudaGetSymbolAddress) and caches it per device; a call during stream capture uses
+ * the cached address, so make the first call on a device before any stream capture.
  * f: device array of n_cells * N^3 elements, updated in place.  Errors: EINVAL,
  * EUNSUPPORTED, ECUDA. */
 boltz_status boltz_relax_noalloc(const boltz_batch* b, void* f, double dt, int steps, void* stream);

@@ -159,15 +159,16 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
-// Cluster barrier that only separates this CTA's reads of its own shared memory from
-// the peers' next writes into it (write-after-read): nothing is published, so the
-// arrive needs no release fence.  Every value read before it has been consumed by the
-// instructions ahead of the arrive (in-order issue, scoreboarded loads), so no read can
-// still be pending when a peer passes the wait.
+// Cluster barrier that separates this CTA's reads of its own shared memory from the
+// peers' next writes into it (write-after-read).  The arrive keeps its default .release
+// semantics: by the PTX memory model that orders every shared-memory load issued before
+// it ahead of any store a peer makes after its matching wait, whatever the compiler and
+// the hardware do with the loads' consumers.  (A relaxed arrive would rely on the loads
+// having completed when the arrive issues, which nothing guarantees.)
 template <int C>
 __device__ __forceinline__ void cluster_barrier_war() {
   if constexpr (C > 1) {
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   } else {
     __syncthreads();
   }
@@ -179,12 +180,12 @@ __device__ __forceinline__ void cluster_barrier_war() {
 template <int C>
 __device__ __forceinline__ void cluster_arrive_war() {
   static_assert(C > 1, "cluster only");
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
 template <int C>
 __device__ __forceinline__ void cluster_wait_war() {
   static_assert(C > 1, "cluster only");
-  asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 template <int C, typename P>
