@@ -266,12 +266,13 @@ def cpu_oracle_rate(wl: dict, budget_s: float, max_cells: int = 4096, first: int
 
 
 def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_bytes: int = 2 << 30,
-                term_groups=None) -> dict:
+                term_groups=None, batch_frac: float = 0.2) -> dict:
     """Serving load (continuous batching through boltz_server_*): Poisson arrivals at
-    `rate` req/s for `seconds`; each request is one cell relaxing for U{10..200} forward
-    Euler steps, N in {16 (60 %), 32 (35 %), 64 (5 %)}, gamma = 1, M = 64, dt = 0.0025,
-    float32 path, admission by an HBM budget.  Latency = completion seen by the host -
-    arrival."""
+    `rate` req/s for `seconds`; each request relaxes for U{10..200} forward Euler steps on
+    N in {16 (60 %), 32 (35 %), 64 (5 %)}, gamma = 1, M = 64, dt = 0.0025, float32 path;
+    a fraction batch_frac of the requests are batches of U{2..8} cells, the others single
+    cells; admission by an HBM budget that holds every job's distributions and term-group
+    scratch.  Latency = completion seen by the host - arrival."""
     import torch
 
     from paper_1608_08009_gb300 import boltz as B
@@ -283,6 +284,7 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
     sizes = rng.choice([16, 32, 64], size=n_req, p=[0.60, 0.35, 0.05])
     steps = rng.integers(10, 201, size=n_req)
+    ncell = np.where(rng.uniform(size=n_req) < batch_frac, rng.integers(2, 9, size=n_req), 1)
     # 16^3 jobs on [-6, 6)^3 (dv = 0.75), 32^3 and 64^3 jobs on [-8, 8)^3 (dv = 0.5, 0.25)
     Ls = {16: 6.0, 32: 8.0, 64: 8.0}
     # term groups: a job's separated terms spread over several clusters, fixed per grid so
@@ -292,14 +294,14 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     stream = torch.cuda.current_stream()
     server = B.Server([grids[16], grids[32], grids[64]], B.BOLTZ_FP32_FFT, 0.0025, budget_bytes, stream)
     reqs = []
+    first = np.concatenate([[0], np.cumsum(ncell)[:-1]])
+    total_cells = int(ncell.sum())
     for k in range(n_req):
         N = int(sizes[k])
-        if N not in grids:
-            reqs.append(None)
-            continue
-        f = W.two_maxwellians(n_req, N, Ls[N], seed, cells=[k])[0].astype(np.float32).ravel()
+        cells = range(int(first[k]), int(first[k] + ncell[k]))
+        f = W.two_maxwellians(total_cells, N, Ls[N], seed, cells=cells).astype(np.float32).ravel()
         reqs.append((torch.from_numpy(f).pin_memory(), torch.empty(f.size, dtype=torch.float32).pin_memory()))
-    # warm-up of both grids outside the measured window
+    # warm-up of every grid outside the measured window
     for N in (16, 32, 64):
         f = torch.zeros(N ** 3, dtype=torch.float32).pin_memory() + 1e-3
         o = torch.empty_like(f)
@@ -309,15 +311,15 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
     torch.cuda.synchronize()
     done_t = [None] * n_req
     ids = [None] * n_req
-    nxt, n_steps, max_res, max_q = 0, 0, 0, 0
+    nxt, n_steps, max_res, max_q, peak_used = 0, 0, 0, 0, 0
     t0 = time.perf_counter()
     pending = set()
     while True:
         now = time.perf_counter() - t0
         while nxt < n_req and arrivals[nxt] <= now:
-            if reqs[nxt] is not None:
-                ids[nxt] = server.submit(gidx[int(sizes[nxt])], reqs[nxt][0], reqs[nxt][1], int(steps[nxt]))
-                pending.add(nxt)
+            ids[nxt] = server.submit(gidx[int(sizes[nxt])], reqs[nxt][0], reqs[nxt][1], int(steps[nxt]),
+                                     int(ncell[nxt]))
+            pending.add(nxt)
             nxt += 1
         # non-blocking: every grid with room (two iterations in flight at most) advances
         res, q, launched = server.pump()
@@ -337,16 +339,19 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
         if now > seconds + 120.0:
             break
     wall = time.perf_counter() - t0
+    stats = server.stats()
     B.boltz_stream_status(stream)
+
+    def pct(sel):
+        ln = np.array([done_t[k] - arrivals[k] for k in range(n_req) if done_t[k] is not None and sel(k)])
+        if not ln.size:
+            return None
+        return {"jobs": int(ln.size), "p50_s": float(np.percentile(ln, 50)), "p99_s": float(np.percentile(ln, 99))}
+
     lat = np.array([done_t[k] - arrivals[k] for k in range(n_req) if done_t[k] is not None])
-    by_n = {}
-    for N in (16, 32, 64):
-        ln = np.array([done_t[k] - arrivals[k] for k in range(n_req) if done_t[k] is not None and sizes[k] == N])
-        if ln.size:
-            by_n[str(N)] = {"jobs": int(ln.size), "p50_s": float(np.percentile(ln, 50)),
-                            "p99_s": float(np.percentile(ln, 99))}
+    by_n = {str(N): pct(lambda k, N=N: sizes[k] == N) for N in (16, 32, 64)}
     served = [k for k in range(n_req) if done_t[k] is not None]
-    cell_steps = int(sum(int(steps[k]) for k in served))
+    cell_steps = int(sum(int(steps[k]) * int(ncell[k]) for k in served))
     server.close()
     for g in grids.values():
         g.close()
@@ -354,12 +359,14 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
             "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
             "mean_latency_s": float(lat.mean()) if lat.size else None,
             "completed": len(served), "by_size": by_n,
-            "unfinished": int(sum(1 for k in range(n_req) if reqs[k] is not None and done_t[k] is None)),
+            "single_cell": pct(lambda k: ncell[k] == 1), "batch": pct(lambda k: ncell[k] > 1),
+            "unfinished": int(sum(1 for k in range(n_req) if done_t[k] is None)),
             "offered_req_per_s": rate, "arrival_window_s": seconds, "wall_s": wall,
             "cell_collisions_per_s": cell_steps / wall, "grid_iterations": n_steps,
-            "max_resident": max_res, "max_queued": max_q, "hbm_budget_bytes": budget_bytes,
-            "mix": "N=16 (L=6): 60 %, N=32 (L=8): 35 %, N=64 (L=8): 5 %; steps U{10..200}; M=64; "
-                   "gamma=1; dt=0.0025; f32",
+            "max_resident_jobs": max_res, "max_queued_jobs": max_q, "hbm_budget_bytes": budget_bytes,
+            "server_reserved_bytes": stats["reserved_bytes"], "server_peak_used_bytes": stats["peak_used_bytes"],
+            "mix": "N=16 (L=6): 60 %, N=32 (L=8): 35 %, N=64 (L=8): 5 %; steps U{10..200}; "
+                   f"{int(round(100 * batch_frac))} % batches of U{{2..8}} cells; M=64; gamma=1; dt=0.0025; f32",
             "term_groups": {str(k): v for k, v in term_groups.items()}}
 
 

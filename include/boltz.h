@@ -275,36 +275,56 @@ boltz_status boltz_relax_indexed(const boltz_batch* b, void* f, const int64_t* c
                                  double dt, int steps, void* stream);
 
 /* ---- Serving: continuous batching of relaxation jobs ------------------------------------
- * A job is one cell relaxing under df/dt = Q(f) (Sec. 3.1, Eq. relax) for `steps` forward
- * Euler steps of size dt with the projection after each step (each step projects onto
- * the moments the cell has at that step).  The server keeps admitted jobs resident in
- * per-grid device pools of float32 slots, admits queued jobs in arrival order while a
- * slot and the HBM budget (bytes of resident f over all grids) allow, advances all
- * resident jobs of a grid by one indexed launch per iteration, and copies each finished
- * job back to its host buffer asynchronously.  A job's result does not depend on which
- * other jobs are resident.  Every grid has its own stream (ordered after the work queued
- * on `stream` at creation) and at most two iterations in flight, so grids advance at
- * their own pace.  Calls are not thread-safe.
+ * A job is a batch of n_cells cells of one grid (one cell for boltz_server_submit), each
+ * relaxing under df/dt = Q(f) (Sec. 3.1, Eq. relax) for `steps` forward Euler steps of
+ * size dt with the projection after each step (each step projects onto the moments the
+ * cell has at that step).  The server makes ONE device allocation of hbm_budget_bytes
+ * and carves everything it uses on the device out of it: the grids' index lists and,
+ * per admitted job, its float32 distributions plus, on grids with term_groups G > 1, its
+ * term-group scratch ((G + 1) N^3 floats per cell).  A job is admitted when those regions
+ * fit, so the device memory the server holds never exceeds the budget.  Queues are per
+ * grid, first come first served within a grid: a job that does not fit yet waits without
+ * holding back the other grids.  All resident cells of a grid advance by one indexed
+ * launch per iteration; each finished job is copied back to its host buffer
+ * asynchronously and its regions return to the arena when that copy completes.  A job's
+ * result does not depend on which other jobs are resident.  Every grid has its own
+ * stream (ordered after the work queued on `stream` at creation) and at most two
+ * iterations in flight, so grids advance at their own pace.  Calls are not thread-safe.
  *   create: grids (one per grid shape a job may use, kept alive by the caller), prec,
- *           dt, budget.  Allocates one pool of budget bytes per grid.
- *   submit: f_host, out_host: N^3 floats each (pinned memory recommended), owned by the
- *           caller until poll reports the job done; returns a job id.
+ *           dt, budget.  EINVAL if the budget cannot hold one cell of every grid (with
+ *           its scratch and the index lists); ENOMEM if the allocation fails.
+ *   submit / submit_batch: f_host, out_host: n_cells * N^3 floats each (pinned memory
+ *           recommended), owned by the caller until poll reports the job done; returns a
+ *           job id.  EINVAL for a job larger than the budget can ever hold.
  *   step:   admission, then one iteration (one step of every resident job, retirement of
  *           the finished ones) for every grid with resident jobs, waiting where a grid
- *           already has two iterations in flight; reports counts.
+ *           already has two iterations in flight; reports counts (jobs).
  *   pump:   as step, but never waits: a grid with two iterations in flight is skipped;
  *           n_launched = iterations issued (nullable).  For serving loops.
- *   poll:   done = 1 once out_host holds the result. */
+ *   poll:   done = 1 once out_host holds the result.
+ *   stats:  reserved (= the budget), used and peak used bytes of the arena, resident
+ *           cells and jobs, queued jobs. */
 typedef struct boltz_server_s* boltz_server;
+typedef struct {
+  size_t reserved_bytes;   /* device bytes the server holds: the budget */
+  size_t used_bytes;       /* of those, in index lists and admitted jobs' regions */
+  size_t peak_used_bytes;  /* largest used_bytes so far */
+  int64_t resident_cells;
+  int64_t resident_jobs;
+  int64_t queued_jobs;
+} boltz_server_stats;
 boltz_status boltz_server_create(const boltz_grid* grids, int n_grids, int prec, double dt,
                                  size_t hbm_budget_bytes, void* stream, boltz_server* out);
 boltz_status boltz_server_submit(boltz_server s, int grid_index, const float* f_host, float* out_host,
                                  int steps, int64_t* job_id);
+boltz_status boltz_server_submit_batch(boltz_server s, int grid_index, const float* f_host, float* out_host,
+                                       int64_t n_cells, int steps, int64_t* job_id);
 boltz_status boltz_server_step(boltz_server s, int* n_resident, int* n_queued);
 boltz_status boltz_server_pump(boltz_server s, int* n_resident, int* n_queued, int* n_launched);
 boltz_status boltz_server_poll(boltz_server s, int64_t job_id, int* done);
-/* Checkpoint of one job: f_host (N^3 floats) receives the job's state after every
- * iteration issued for it so far, *remaining_steps the steps still to run (0 once
+boltz_status boltz_server_stats_get(boltz_server s, boltz_server_stats* out);
+/* Checkpoint of one job: f_host (n_cells * N^3 floats) receives the job's state after
+ * every iteration issued for it so far, *remaining_steps the steps still to run (0 once
  * finished).  Synchronises the job's grid stream.  The state plus the remaining steps is
  * all a job needs: submitting them to any server with the same grid continues the job
  * and gives the same bits as an uninterrupted run. */

@@ -37,7 +37,8 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_collide_indexed", "boltz_relax_indexed", "boltz_server_create", "boltz_server_submit",
             "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
             "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
-            "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_host_chunks")
+            "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_host_chunks",
+            "boltz_server_submit_batch", "boltz_server_stats_get")
 
 
 class BoltzError(RuntimeError):
@@ -55,6 +56,12 @@ class boltz_grid_opts(ctypes.Structure):
 class boltz_batch(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_void_p), ("n_cells", ctypes.c_int64), ("prec", ctypes.c_int),
                 ("f_is_fp64", ctypes.c_int)]
+
+
+class boltz_server_stats(ctypes.Structure):
+    _fields_ = [("reserved_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("peak_used_bytes", ctypes.c_size_t), ("resident_cells", ctypes.c_int64),
+                ("resident_jobs", ctypes.c_int64), ("queued_jobs", ctypes.c_int64)]
 
 
 class boltz_group(ctypes.Structure):
@@ -97,6 +104,8 @@ def lib() -> ctypes.CDLL:
         L.boltz_relax_indexed.argtypes = [P(boltz_batch), vp, vp, i64, f64, i32, vp]
         L.boltz_server_create.argtypes = [P(vp), i32, i32, f64, ctypes.c_size_t, vp, P(vp)]
         L.boltz_server_submit.argtypes = [vp, i32, vp, vp, i32, P(i64)]
+        L.boltz_server_submit_batch.argtypes = [vp, i32, vp, vp, i64, i32, P(i64)]
+        L.boltz_server_stats_get.argtypes = [vp, P(boltz_server_stats)]
         L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
         L.boltz_server_pump.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.boltz_server_checkpoint.argtypes = [vp, i64, vp, P(i32)]
@@ -115,7 +124,8 @@ def lib() -> ctypes.CDLL:
                      "boltz_server_create", "boltz_server_submit", "boltz_server_step", "boltz_server_poll",
                      "boltz_server_destroy", "boltz_relax_host", "boltz_plan_create", "boltz_plan_run",
                      "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump",
-                     "boltz_create_grid2d", "boltz_server_checkpoint"):
+                     "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_server_submit_batch",
+                     "boltz_server_stats_get"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -250,7 +260,8 @@ def boltz_grid_tables(grid: int, M_dirs: int, dim: int = 3):
 
 
 class Server:
-    """Continuous-batching relaxation server (boltz_server_*): one pool per grid."""
+    """Continuous-batching relaxation server (boltz_server_*): one device arena of the HBM
+    budget holds every admitted job's state and scratch."""
 
     def __init__(self, grids, prec: int, dt: float, hbm_budget_bytes: int, stream=None):
         arr = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
@@ -260,12 +271,18 @@ class Server:
         self.handle = h.value
         self._keep = []  # host buffers stay alive until their job is done
 
-    def submit(self, grid_index: int, f_host, out_host, steps: int) -> int:
+    def submit(self, grid_index: int, f_host, out_host, steps: int, n_cells: int = 1) -> int:
+        """Queue a job of n_cells cells (f_host, out_host: n_cells * N^3 floats)."""
         jid = ctypes.c_int64()
-        _check(lib().boltz_server_submit(self.handle, grid_index, _ptr(f_host), _ptr(out_host), steps,
-                                         ctypes.byref(jid)))
+        _check(lib().boltz_server_submit_batch(self.handle, grid_index, _ptr(f_host), _ptr(out_host), n_cells,
+                                               steps, ctypes.byref(jid)))
         self._keep.append((f_host, out_host))
         return jid.value
+
+    def stats(self) -> dict:
+        st = boltz_server_stats()
+        _check(lib().boltz_server_stats_get(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in boltz_server_stats._fields_}
 
     def step(self):
         r, q = ctypes.c_int(), ctypes.c_int()

@@ -245,6 +245,18 @@ int cluster_choices(int N, int prec, int* out) {
   return k;
 }
 
+int launch_groups(const boltz_grid_s* g, int prec, int groups) {
+  const bool tc = (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XBF16_DFT || prec == BOLTZ_3XTF32_DFT);
+  if (g->dim == 2 || tc) return 1;
+  const int G = groups < 0 ? g->term_groups : groups;
+  return std::max(1, std::min(G, g->M_eff));
+}
+
+size_t split_block_bytes(const boltz_grid_s* g, int G, int prec) {
+  const size_t tsz = (prec == BOLTZ_FP64) ? sizeof(double) : sizeof(float);
+  return ((size_t)(G + 1) * cell_points(g) * tsz + sizeof(unsigned) + kSplitUnit - 1) / kSplitUnit * kSplitUnit;
+}
+
 // Scratch of split launches: [cells] arrival counters (zeroed once; every launch leaves
 // them at zero), then the partial gains [cells][G][n] and the loss multipliers [cells][n].
 boltz_status ensure_split_scratch(const boltz_grid_s* g, int64_t n_cells, int G, int prec, cudaStream_t stream) {
@@ -273,7 +285,8 @@ boltz_status ensure_split_scratch(const boltz_grid_s* g, int64_t n_cells, int G,
 boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, int f_is_fp64, const void* f_in,
                             const void* f_base, void* out, double a, double b, double s, double* Utgt,
                             int compute_targets, int project, cudaStream_t stream, const int64_t* cell_idx,
-                            int64_t pool_cells, int groups, int cluster) {
+                            int64_t pool_cells, int groups, int cluster, const int64_t* split_idx,
+                            void* split_base) {
   if (n_cells == 0) return BOLTZ_OK;
   if (!collide_supported_grid(g, prec)) {
     set_error("unsupported (N, precision) combination");
@@ -303,8 +316,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   }
   if (cluster == 0 && prec != BOLTZ_FP64) cluster = g->cluster_size;  // 0: the default of (N, prec)
   const bool tc = (prec == BOLTZ_TF32_DFT || prec == BOLTZ_3XBF16_DFT || prec == BOLTZ_3XTF32_DFT);
-  int G = tc ? 1 : (groups < 0 ? g->term_groups : groups);
-  G = std::max(1, std::min(G, g->M_eff));
+  const int G = launch_groups(g, prec, groups);
   if (n_cells * (int64_t)G * 16 > (int64_t)INT32_MAX) {
     set_error("n_cells * term_groups too large for one launch");
     return BOLTZ_EINVAL;
@@ -312,11 +324,11 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   const size_t n = (size_t)g->N * g->N * g->N;
   const size_t tsz = (prec == BOLTZ_FP64) ? sizeof(double) : sizeof(float);
   const size_t cnt_bytes = ((size_t)n_cells * sizeof(unsigned) + 255) / 256 * 256;
-  if (G > 1) {
+  if (G > 1 && !split_idx) {
     boltz_status r = ensure_split_scratch(g, n_cells, G, prec, stream);
     if (r != BOLTZ_OK) return r;
   }
-  CollideArgs args;
+  CollideArgs args = {};
   args.f_in = f_in;
   args.f_base = f_base;
   args.out = out;
@@ -334,10 +346,20 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.geom.dv = g->dv;
   for (int i = 0; i < 25; ++i) args.geom.G[i] = g->proj.G[i];
   args.groups = G;
-  char* sb = static_cast<char*>(g->split_buf);
-  args.arrivals = (G > 1) ? reinterpret_cast<unsigned*>(sb) : nullptr;
-  args.part = (G > 1) ? sb + cnt_bytes : nullptr;
-  args.loss = (G > 1) ? sb + cnt_bytes + (size_t)n_cells * G * n * tsz : nullptr;
+  args.split_idx = nullptr;
+  args.split_unit = 0;
+  if (G > 1 && split_idx) {
+    args.split_idx = split_idx;
+    args.split_unit = kSplitUnit;
+    args.part = split_base;
+    args.loss = nullptr;
+    args.arrivals = nullptr;
+  } else {
+    char* sb = static_cast<char*>(g->split_buf);
+    args.arrivals = (G > 1) ? reinterpret_cast<unsigned*>(sb) : nullptr;
+    args.part = (G > 1) ? sb + cnt_bytes : nullptr;
+    args.loss = (G > 1) ? sb + cnt_bytes + (size_t)n_cells * G * n * tsz : nullptr;
+  }
   if (prec == BOLTZ_FP64) {
     args.tab = g->tab64;
     return dispatch_3d_f64(g, args, n_cells, stream, cluster, f_is_fp64);

@@ -268,6 +268,24 @@ __device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, dou
   re[0] = v.x; im[0] = v.y;
 }
 
+// Term-group scratch of launch cell lc: partial gains [G][n], loss multipliers [n] and
+// the cell's arrival count, by launch position or through the block index of
+// CollideArgs::split_idx.
+template <typename T>
+__device__ __forceinline__ void split_scratch(const CollideArgs& args, long long lc, int G, int n, T*& part,
+                                              T*& lossp, unsigned*& arr) {
+  if (args.split_idx) {
+    char* blk = static_cast<char*>(args.part) + (size_t)args.split_idx[lc] * args.split_unit;
+    part = reinterpret_cast<T*>(blk);
+    lossp = part + (size_t)G * n;
+    arr = reinterpret_cast<unsigned*>(lossp + n);
+  } else {
+    part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
+    lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+    arr = args.arrivals + lc;
+  }
+}
+
 // Projection of Sec. 3.2 (Eq. minim1) for one cell owned by a cluster: m[5] is this
 // thread's share of Phi g; red holds [WARPS][5] scratch, then [5] Phi g and [5] Phi f_in
 // (the targets, when computed) of this CTA.  Returns c5 = G (U - Phi g), zero without
@@ -614,9 +632,10 @@ collide_kernel(const CollideArgs args) {
     tc.phase = 0u;
   }
   // asynchronous scatter (32^3, 4 CTAs per SM): the owner's mbarrier counts the bytes
-  // that reach its x-plane buffer; it is armed for term 0 before the barrier that ends
-  // the forward transform and re-armed for term i + 1 before the write-after-read
-  // barrier of term i, so no bytes of a term can arrive before their phase is armed
+  // that reach its x-plane buffer; it is armed for term 0 at initialisation (before this
+  // CTA's first write-after-read arrive) and re-armed for term i + 1 right after the wait
+  // for term i (before the arrive of term i), so no bytes of a term can arrive before
+  // their phase is armed
   constexpr bool kAsync = Cfg::kAsyncScatter;
   const uint32_t scat_mbar = smem_u32(smem_raw + Cfg::OFF_FLAG + 16);
   uint32_t scat_phase = 0;
@@ -624,6 +643,7 @@ collide_kernel(const CollideArgs args) {
     if (threadIdx.x == 0) {
       mbar_init(scat_mbar, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);  // term 0's phase, armed before any arrive
     }
   }
   // inverse 1D transform of this thread's pencil: register FFT or tensor-core DFT
@@ -701,6 +721,11 @@ collide_kernel(const CollideArgs args) {
         ld_local_chunk(src, re + c * VEC, im + c * VEC);
       }
     }
+    // Single buffer: the peers must be done gathering from this CTA's x-planes before
+    // the first scatter into them.  In a cluster the barrier is split: this arrive, right
+    // after the last gather (a release: it orders the gathers before the peers' stores),
+    // and the wait inside the first kx pass just before its stores.
+    if constexpr (Cfg::NXB == 1 && C > 1) cluster_arrive_war<C>();
     fft_regs<N, -1>(re, im);
     const T scale = T(1) / T(n);
     const bool nyq = (ky_own == N / 2) || (kzt == N / 2);
@@ -728,18 +753,9 @@ collide_kernel(const CollideArgs args) {
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
   }
-  if constexpr (kAsync) {
-    if (threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
-  }
-  // Single buffer: the peers must be done reading this CTA's x-planes before the first
-  // scatter.  In a cluster the barrier is split: this arrive, and the wait inside the
-  // first kx pass just before its stores, so the transform runs meanwhile.
+  // Single buffer without a cluster: the CTA's own gathers end before its first scatter.
   constexpr bool kSplitWar = (Cfg::NXB == 1) && (C > 1);
-  if constexpr (kSplitWar) {
-    cluster_arrive_war<C>();
-  } else if constexpr (Cfg::NXB == 1) {
-    cluster_barrier<C>();
-  }
+  if constexpr (Cfg::NXB == 1 && C == 1) __syncthreads();
 
   // ---- angular loop: one complex inverse transform per separated term --------------
   T acc[N];
@@ -806,14 +822,20 @@ collide_kernel(const CollideArgs args) {
     for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
   };
   // pass along ky: thread (xl, z); outputs along y.  accumulate: Q+ += w Re Im; otherwise
-  // re[] keeps the loss multiplier L(v) along y.
-  auto pass_ky = [&](const T2* XB, T wj, bool accumulate) {
+  // re[] keeps the loss multiplier L(v) along y.  release: these loads are this CTA's
+  // last reads of its x-plane buffer for the term, so the write-after-read arrive (a
+  // release, which orders them before the peers' next stores) follows them directly and
+  // the transform runs after it.
+  auto pass_ky = [&](const T2* XB, T wj, bool accumulate, bool release) {
     const T2* col = XB + Cfg::elem(xlt, 0, zt);
 #pragma unroll
     for (int ky = 0; ky < N; ++ky) {
       const T2 v = col[ky * (RW_ * VEC)];
       re[ky] = v.x;
       im[ky] = v.y;
+    }
+    if constexpr (Cfg::NXB == 1 && C > 1) {
+      if (release) cluster_arrive_war<C>();
     }
     inverse_1d();
     if (accumulate) {
@@ -839,7 +861,7 @@ collide_kernel(const CollideArgs args) {
       T2* XBj = XB0 + ((i + 1) & 1) * Cfg::XB;
       const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
       pass_kx(j, XBj);
-      if (i > 0) pass_ky(XB0 + (i & 1) * Cfg::XB, w_prev, true);
+      if (i > 0) pass_ky(XB0 + (i & 1) * Cfg::XB, w_prev, true, false);
       cluster_barrier<C>();
       pass_kz(XBj);
       __syncthreads();
@@ -847,35 +869,33 @@ collide_kernel(const CollideArgs args) {
     }
     // last term: the loss transform (re[] keeps L) or a gain term
     if (has_loss) {
-      pass_ky(XB0 + (nt & 1) * Cfg::XB, T(0), false);
+      pass_ky(XB0 + (nt & 1) * Cfg::XB, T(0), false, false);
     } else {
-      pass_ky(XB0 + (nt & 1) * Cfg::XB, w_prev, true);
+      pass_ky(XB0 + (nt & 1) * Cfg::XB, w_prev, true, false);
     }
   } else {
     for (int i = 0; i < nt; ++i) {
       const int j = kSplit ? ((j0 + i < j1) ? j0 + i : M_eff) : i;
       const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
       pass_kx(j, XB0);
+      const bool more = (i < nt - 1);
       if constexpr (kAsync) {
         // every producer's bytes of this term have landed in this CTA's buffer
         if (!mbar_wait(scat_mbar, scat_phase)) atomicOr(&g_boltz_status, kStatusTimeout);
         scat_phase ^= 1u;
+        // arm the next term's phase now: its bytes cannot come before this CTA's
+        // write-after-read arrive below
+        if (more && threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
       } else {
         cluster_barrier<C>();
       }
       pass_kz(XB0);
       __syncthreads();
-      pass_ky(XB0, wj, j < M_eff);
-      if (i < nt - 1) {
-        if constexpr (kAsync) {
-          if (threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
-        }
-        // single buffer: owners done before the next scatter (its wait is in pass_kx)
-        if constexpr (kSplitWar) {
-          cluster_arrive_war<C>();
-        } else {
-          cluster_barrier_war<C>();
-        }
+      // single buffer: the owners' last reads of term i (the ky loads) come before the
+      // arrive that lets the peers scatter term i + 1 (their wait is in pass_kx)
+      pass_ky(XB0, wj, j < M_eff, more && kSplitWar);
+      if constexpr (!kSplitWar) {
+        if (more) cluster_barrier_war<C>();
       }
     }
     if constexpr (kSplitWar) {
@@ -902,8 +922,10 @@ collide_kernel(const CollideArgs args) {
     // of the cell (fence, barrier, one atomic: no waiting).  The cluster that arrives last
     // sums the G partials in group order, so the result does not depend on the order of
     // arrival, and continues with the epilogue; the others leave.
-    T* part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
-    T* lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+    T* part;
+    T* lossp;
+    unsigned* arrp;
+    split_scratch<T>(args, lc, G, n, part, lossp, arrp);
 #pragma unroll
     for (int y = 0; y < N; ++y) {
       const int idx = (x_own * N + y) * N + zt;
@@ -914,9 +936,9 @@ collide_kernel(const CollideArgs args) {
     cluster_barrier<C>();
     unsigned* flag = reinterpret_cast<unsigned*>(smem_raw + Cfg::OFF_FLAG);
     if (rank == 0 && t == 0) {
-      const unsigned prev = atomicAdd(&args.arrivals[lc], 1u);
+      const unsigned prev = atomicAdd(arrp, 1u);
       const unsigned last = (prev == (unsigned)(G - 1)) ? 1u : 0u;
-      if (last) args.arrivals[lc] = 0u;  // every group has arrived: ready for the next launch
+      if (last) *arrp = 0u;  // every group has arrived: ready for the next launch
 #pragma unroll
       for (int q = 0; q < C; ++q) *cta_smem<C>(flag, q) = last;
     }
@@ -1212,8 +1234,10 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   float* acc_row = accs + (size_t)xlt * N * N + z;  // acc_row[y * N], this thread's (x, z) row
   if constexpr (kSplit) {
     // partial gain and loss of this group, then the last-arrival count (as collide_kernel)
-    T* part = reinterpret_cast<T*>(args.part) + (size_t)lc * G * n;
-    T* lossp = reinterpret_cast<T*>(args.loss) + (size_t)lc * n;
+    T* part;
+    T* lossp;
+    unsigned* arrp;
+    split_scratch<T>(args, lc, G, n, part, lossp, arrp);
 #pragma unroll
     for (int y = 0; y < N; ++y) {
       const int idx = (x * N + y) * N + z;
@@ -1224,9 +1248,9 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
     cluster_barrier<C>();
     unsigned* flag = reinterpret_cast<unsigned*>(smem_raw + Cfg::OFF_FLAG);
     if (rank == 0 && t == 0) {
-      const unsigned prev = atomicAdd(&args.arrivals[lc], 1u);
+      const unsigned prev = atomicAdd(arrp, 1u);
       const unsigned last = (prev == (unsigned)(G - 1)) ? 1u : 0u;
-      if (last) args.arrivals[lc] = 0u;
+      if (last) *arrp = 0u;
 #pragma unroll
       for (int q = 0; q < C; ++q) *cta_smem<C>(flag, q) = last;
     }

@@ -49,6 +49,12 @@ struct CollideArgs {
   void* part;          // [cells][G][n] T
   void* loss;          // [cells][n] T
   unsigned* arrivals;  // [cells], zero between launches
+  // Term-group scratch by block instead of by launch position (serving loop): when
+  // split_idx is non-null, cell c of the launch uses the block at part + split_idx[c] *
+  // split_unit bytes, laid out as [G][n] T partial gains, [n] T loss multipliers, one
+  // unsigned arrival count (zero between launches); loss and arrivals are then unused.
+  const int64_t* split_idx;
+  size_t split_unit;
   KernelGeom geom;
 };
 
@@ -115,7 +121,15 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                             const void* f_in, const void* f_base, void* out, double a, double b,
                             double s, double* Utgt, int compute_targets, int project,
                             cudaStream_t stream, const int64_t* cell_idx = nullptr,
-                            int64_t pool_cells = 0, int groups = -1, int cluster = 0);
+                            int64_t pool_cells = 0, int groups = -1, int cluster = 0,
+                            const int64_t* split_idx = nullptr, void* split_base = nullptr);
+// Bytes of one term-group scratch block (CollideArgs::split_idx) of grid g with G groups:
+// a multiple of kSplitUnit.  split_idx entries passed to launch_collide count kSplitUnit
+// bytes from split_base.
+constexpr size_t kSplitUnit = 16;
+size_t split_block_bytes(const boltz_grid_s* g, int G, int prec);
+// Term groups a launch of grid g in precision prec uses (groups < 0: the grid's setting).
+int launch_groups(const boltz_grid_s* g, int prec, int groups);
 // groups < 0: the grid's term_groups; cluster 0: the default cluster size of (N, prec)
 int default_cluster(int N, int prec);
 // Grow the grid's scratch of split launches (term groups) to n_cells cells of G groups;

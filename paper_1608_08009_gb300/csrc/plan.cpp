@@ -6,8 +6,8 @@
 // lengths), so a ragged step is one kernel launch per group.  The plan makes the whole
 // step loop a single CUDA graph: every group's launches form one branch, branches run
 // concurrently, and the host pays one graph launch per call.  Before capture an optional
-// autotuner times every (term groups, cluster size) candidate of each group on a copy of
-// its cells and keeps the fastest.
+// autotuner chooses each group's (term groups, cluster size) by timing the concurrent step
+// (below).
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -39,6 +39,7 @@ struct boltz_plan_s {
   cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  double tuned_step_us = 0.0;  // the autotuner's last whole-step time (0 without tuning)
 };
 
 using boltz::set_error;
@@ -64,73 +65,182 @@ static void free_plan(boltz_plan_s* p) {
   delete p;
 }
 
-// Time one relaxation launch of every candidate on a copy of the group's cells (the
-// user's f is not touched) and keep the fastest.  Term groups are only tried when the
-// cells alone leave SMs idle.
-static boltz_status autotune(PlanGroup& g, cudaStream_t s) {
-  const size_t n = boltz::cell_points(g.grid);
-  const size_t bytes = (size_t)g.n_cells * n * (g.f_is_fp64 ? 8 : 4);
-  void *fa = nullptr, *qa = nullptr;
-  cudaError_t e;
-  if (cudaMalloc(&fa, bytes) != cudaSuccess || cudaMalloc(&qa, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(fa);
-    set_error("autotune scratch allocation failed");
-    return BOLTZ_ENOMEM;
-  }
-  boltz_status st = BOLTZ_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+// Autotuning.  A candidate is (term groups, cluster size) for one group.  Every group's
+// candidates are first timed alone, one launch on a copy of its cells (the user's f is
+// not touched; term groups only while the cells alone leave SMs idle), and the three
+// fastest are kept.  Timing groups alone favours parallelism inside a group, but in the
+// graph the groups run concurrently and share the SMs, so the choice is then refined on
+// the step itself: starting from the grids' own settings, the groups are visited in
+// order of their time alone (slowest first), each kept candidate is tried with the other
+// groups fixed, and it is adopted only if the whole concurrent step gets faster by more
+// than 1 %.  The result is never slower than the untuned plan beyond timing noise.
+namespace {
+
+struct Cand {
+  int G = 1, cluster = 0;
+  float ms = 0.f;  // one launch of the group alone
+};
+
+struct TuneCopies {
+  void* fa = nullptr;  // copy of the group's f (input of every timed launch)
+  void* qa = nullptr;  // output of the timed launches
+};
+
+constexpr int kKeep = 3;          // candidates kept per group after timing alone
+constexpr int kStepEvals = 48;    // whole-step timings at most
+constexpr float kGain = 0.99f;    // adopt a candidate only if the step gets 1 % faster
+
+boltz_status launch_candidate(const PlanGroup& g, const TuneCopies& c, const Cand& k, cudaStream_t s) {
+  return boltz::launch_collide(g.grid, g.n_cells, g.prec, g.f_is_fp64, c.fa, nullptr, c.qa, 0.0, 1.0, 1e-3, g.U0, 1,
+                               1, s, nullptr, 0, k.G, k.cluster);
+}
+
+boltz_status time_alone(const PlanGroup& g, const TuneCopies& c, int sms, cudaStream_t s, cudaEvent_t e0,
+                        cudaEvent_t e1, std::vector<Cand>& out) {
   int cl[4];
   const int ncl = boltz::cluster_choices(g.grid->N, g.prec, cl);
-  double best = 1e300;
-  if ((e = cudaMemcpyAsync(fa, g.f, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
-      (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
-    st = plan_fail(e, "autotune setup");
-    goto done;
-  }
+  cudaError_t e = cudaSuccess;
   for (int ci = 0; ci < ncl; ++ci) {
     for (int G = 1; G <= std::min(16, g.grid->M_eff); G *= 2) {
       if (G > 1 && g.n_cells * cl[ci] * (G / 2) >= 2 * (int64_t)sms) break;  // the GPU is already full
-      float ms = 0.f, best_c = 1e30f;
+      Cand k;
+      k.G = G;
+      k.cluster = cl[ci];
+      float best = 1e30f, ms = 0.f;
+      boltz_status st = BOLTZ_OK;
       for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up (and sizes the split scratch)
         if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
-        st = boltz::launch_collide(g.grid, g.n_cells, g.prec, g.f_is_fp64, fa, nullptr, qa, 0.0, 1.0, 1e-3, g.U0, 1,
-                                   1, s, nullptr, 0, G, cl[ci]);
-        if (st == BOLTZ_EUNSUPPORTED) break;  // not schedulable here: skip the candidate
-        if (st != BOLTZ_OK) goto done;
+        st = launch_candidate(g, c, k, s);
+        if (st != BOLTZ_OK) break;
         if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
             (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
           break;
-        if (rep > 0) best_c = std::min(best_c, ms);
+        if (rep > 0) best = std::min(best, ms);
       }
-      if (e != cudaSuccess) {
-        st = plan_fail(e, "autotune timing");
-        goto done;
-      }
-      if (st == BOLTZ_EUNSUPPORTED) {
-        st = BOLTZ_OK;
-        cudaEventSynchronize(e0);  // the skipped candidate recorded e0 only
+      if (e != cudaSuccess) return plan_fail(e, "autotune timing");
+      if (st == BOLTZ_EUNSUPPORTED) {  // not schedulable here: skip the cluster size
+        cudaEventSynchronize(e0);        // the skipped candidate recorded e0 only
         break;
       }
-      if (best_c < best) {
-        best = best_c;
-        g.term_groups = G;
-        g.cluster = cl[ci];
-      }
+      if (st != BOLTZ_OK) return st;
+      k.ms = best;
+      out.push_back(k);
     }
   }
-  g.tuned_us = best * 1000.0;
+  std::sort(out.begin(), out.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+  return BOLTZ_OK;
+}
+
+// One step of every group concurrently (each on its own stream, forked from and joined to
+// s), as the graph runs it; the faster of two runs.
+boltz_status time_step(boltz_plan_s* p, const std::vector<TuneCopies>& copies, const std::vector<Cand>& pick,
+                       cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* out) {
+  cudaError_t e;
+  float best = 1e30f, ms = 0.f;
+  for (int rep = 0; rep < 2; ++rep) {
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess || (e = cudaEventRecord(p->fork, s)) != cudaSuccess)
+      return plan_fail(e, "autotune fork");
+    for (size_t i = 0; i < p->groups.size(); ++i) {
+      PlanGroup& g = p->groups[i];
+      if (g.n_cells == 0) continue;
+      if ((e = cudaStreamWaitEvent(g.stream, p->fork, 0)) != cudaSuccess) return plan_fail(e, "autotune fork");
+      boltz_status st = launch_candidate(g, copies[i], pick[i], g.stream);
+      if (st != BOLTZ_OK) return st;
+      if ((e = cudaEventRecord(g.join, g.stream)) != cudaSuccess || (e = cudaStreamWaitEvent(s, g.join, 0)) != cudaSuccess)
+        return plan_fail(e, "autotune join");
+    }
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+      return plan_fail(e, "autotune timing");
+    best = std::min(best, ms);
+  }
+  *out = best;
+  return BOLTZ_OK;
+}
+
+boltz_status autotune(boltz_plan_s* p, cudaStream_t s) {
+  const size_t ng = p->groups.size();
+  std::vector<TuneCopies> copies(ng);
+  std::vector<std::vector<Cand>> cands(ng);
+  std::vector<Cand> pick(ng);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  boltz_status st = BOLTZ_OK;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    st = plan_fail(e, "autotune setup");
+    goto done;
+  }
+  for (size_t i = 0; i < ng; ++i) {
+    PlanGroup& g = p->groups[i];
+    pick[i].G = g.term_groups;
+    pick[i].cluster = g.cluster;
+    if (g.n_cells == 0) continue;
+    const size_t bytes = (size_t)g.n_cells * boltz::cell_points(g.grid) * (g.f_is_fp64 ? 8 : 4);
+    if (cudaMalloc(&copies[i].fa, bytes) != cudaSuccess || cudaMalloc(&copies[i].qa, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("autotune scratch allocation failed");
+      st = BOLTZ_ENOMEM;
+      goto done;
+    }
+    if ((e = cudaMemcpyAsync(copies[i].fa, g.f, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+      st = plan_fail(e, "autotune copy");
+      goto done;
+    }
+    if ((st = time_alone(g, copies[i], sms, s, e0, e1, cands[i])) != BOLTZ_OK) goto done;
+    if (cands[i].size() > (size_t)kKeep) cands[i].resize(kKeep);
+    // the time alone of the grid's own setting orders the refinement
+    pick[i].ms = 1e30f;
+    for (const Cand& k : cands[i])
+      if (k.G == pick[i].G && k.cluster == pick[i].cluster) pick[i].ms = k.ms;
+    if (pick[i].ms == 1e30f && !cands[i].empty()) pick[i].ms = cands[i].front().ms;
+  }
+  {
+    float base = 0.f;
+    if ((st = time_step(p, copies, pick, s, e0, e1, &base)) != BOLTZ_OK) goto done;  // warm-up
+    if ((st = time_step(p, copies, pick, s, e0, e1, &base)) != BOLTZ_OK) goto done;
+    std::vector<size_t> order;
+    for (size_t i = 0; i < ng; ++i)
+      if (p->groups[i].n_cells > 0) order.push_back(i);
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return pick[x].ms > pick[y].ms; });
+    int evals = 0;
+    for (size_t i : order) {
+      for (const Cand& k : cands[i]) {
+        if (evals >= kStepEvals) break;
+        if (k.G == pick[i].G && k.cluster == pick[i].cluster) continue;
+        std::vector<Cand> trial = pick;
+        trial[i] = k;
+        float t = 0.f;
+        if ((st = time_step(p, copies, trial, s, e0, e1, &t)) != BOLTZ_OK) goto done;
+        ++evals;
+        if (t < kGain * base) {
+          base = t;
+          pick[i] = k;
+        }
+      }
+    }
+    for (size_t i = 0; i < ng; ++i) {
+      p->groups[i].term_groups = pick[i].G;
+      p->groups[i].cluster = pick[i].cluster;
+      p->groups[i].tuned_us = pick[i].ms * 1000.0;
+    }
+    p->tuned_step_us = base * 1000.0;
+  }
 done:
+  cudaStreamSynchronize(s);
+  for (auto& g : p->groups) cudaStreamSynchronize(g.stream);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  cudaStreamSynchronize(s);
-  cudaFree(fa);
-  cudaFree(qa);
+  for (auto& c : copies) {
+    cudaFree(c.fa);
+    cudaFree(c.qa);
+  }
   return st;
 }
+
+}  // namespace
 
 extern "C" {
 
@@ -208,12 +318,12 @@ boltz_status boltz_plan_create(const boltz_group* groups, int n_groups, double d
     free_plan(p);
     return plan_fail(e, "plan sync");
   }
+  if ((flags & BOLTZ_PLAN_AUTOTUNE) && (st = autotune(p, p->cap)) != BOLTZ_OK) {
+    free_plan(p);
+    return st;
+  }
   for (auto& g : p->groups) {
     if (g.n_cells == 0) continue;
-    if ((flags & BOLTZ_PLAN_AUTOTUNE) && (st = autotune(g, p->cap)) != BOLTZ_OK) {
-      free_plan(p);
-      return st;
-    }
     if (g.term_groups > 1 &&
         (st = boltz::ensure_split_scratch(g.grid, g.n_cells, g.term_groups, g.prec, p->cap)) != BOLTZ_OK) {
       free_plan(p);

@@ -302,12 +302,19 @@ def test_full_size_mixed_sampled():
 def test_every_cluster_size_parity(N, L, C):
     """Every cluster size the float32 path dispatches (boltz_grid_opts.cluster_size), each
     against the oracle: collide with float64 and float32 storage, and Euler / Heun relax
-    with one and with two term groups."""
+    with one and with two term groups.
+
+    Relax tolerance: each collision evaluation is within the float32 bound tol of its own
+    input; over two steps (four evaluations for Heun) an evaluation's error also reaches
+    the next one through the linearised operator, whose norm is of the order of the
+    largest loss rate max L, so the increment is held to tol (1 + dt max L)."""
     M, cells = 24, 3
+    dt = 0.004
     f = W.two_maxwellians(cells, N, L, seed=151 + 7 * C)
     og = oracle_grid(N, L, M)
     Qref = O.collide(f, og)
     tol = fp32_tol(f, og)
+    tol_relax = tol * (1.0 + dt * float(np.abs(O.operator.gain_loss(f, og)[1]).max()))
     f32 = f.astype(np.float32).astype(np.float64)
     Qref32 = O.collide(f32, og)
     for groups in (1, 2):
@@ -315,11 +322,11 @@ def test_every_cluster_size_parity(N, L, C):
             assert rel_l2(run_collide(g, f, B.BOLTZ_FP32_FFT), Qref) <= tol
             assert rel_l2(run_collide(g, f.astype(np.float32), B.BOLTZ_FP32_FFT, fp64=False), Qref32) <= tol + EPS32
             for rk in (1, 2):
-                ref = O.relax(f, og, 0.004, 2, rk_order=rk)
+                ref = O.relax(f, og, dt, 2, rk_order=rk)
                 ft = torch.from_numpy(f).cuda()
-                B.boltz_relax(g.batch(cells, B.BOLTZ_FP32_FFT), ft, 0.004, 2, rk)
+                B.boltz_relax(g.batch(cells, B.BOLTZ_FP32_FFT), ft, dt, 2, rk)
                 B.boltz_stream_status()
-                assert rel_l2(ft.cpu().numpy() - f, ref - f) <= tol, (groups, rk)
+                assert rel_l2(ft.cpu().numpy() - f, ref - f) <= tol_relax, (groups, rk)
 
 
 def test_indexed_cells_match_contiguous_batch():
