@@ -298,7 +298,9 @@ boltz_status boltz_relax_indexed(const boltz_batch* b, void* f, const int64_t* c
  *           job id.  EINVAL for a job larger than the budget can ever hold.
  *   step:   admission, then one iteration (one step of every resident job, retirement of
  *           the finished ones) for every grid with resident jobs, waiting where a grid
- *           already has two iterations in flight; reports counts (jobs).
+ *           already has two iterations in flight, and, when a queued job waits for memory,
+ *           for the result copies of finished jobs (which return theirs); reports counts
+ *           (jobs).
  *   pump:   as step, but never waits: a grid with two iterations in flight is skipped;
  *           n_launched = iterations issued (nullable).  For serving loops.
  *   poll:   done = 1 once out_host holds the result.
@@ -330,6 +332,37 @@ boltz_status boltz_server_stats_get(boltz_server s, boltz_server_stats* out);
  * and gives the same bits as an uninterrupted run. */
 boltz_status boltz_server_checkpoint(boltz_server s, int64_t job_id, float* f_host, int* remaining_steps);
 boltz_status boltz_server_destroy(boltz_server s);
+
+/* ---- Fast Kinetic Scheme in one space dimension (Sec. 3.1) ------------------------------
+ * Transport of the piecewise-constant distribution (Eq. transport, Eq. f_bar) coupled to
+ * the collision step at the cell centres (Eq. relax and Eq. f_coll with the rescaled
+ * operator Q / tau of the numerical tests, forward Euler, projected onto the moments of
+ * the transported values, Sec. 3.2).  Cells form rows of n_x cells of width dx along x;
+ * the velocity grid is the batch's grid.  Each x-velocity's intervals move exactly with
+ * v_x; after a time t the centre of cell j lies in the interval that started as cell
+ * j - ceil(v_x t / dx - 1/2), so a step moves each x-velocity's column of centre values
+ * by 0 or +-1 cells, fused into the collision launch's loads: one launch per step, f
+ * read once and the new f written once.  The state holds only the time t (t += dt per
+ * step).
+ *   create:  grid, n_x >= 1, dx > 0.  EUNSUPPORTED for N > 64.
+ *   step:    f_in -> f_out (device, n_cells * N^3 each, n_cells a multiple of n_x,
+ *            out of place: f_out != f_in); inflow_lo / inflow_hi: device [rows][N^3],
+ *            the states left of each row's cell 0 and right of its cell n_x - 1 (fixed
+ *            Dirichlet states, or a neighbouring sub-domain's edge cells at the start
+ *            of the step for a split domain, Sec. 4.2, fig. mpi-decomp).  dt > 0 with
+ *            dt |v_x| <= dx for every grid velocity (Eq. Time; EINVAL otherwise), tau > 0.
+ *            Asynchronous on `stream`; device conditions as boltz_collide.
+ *   time / set_time: the accumulated time (checkpoint and resume).
+ *   shifts:  d[kx] (N ints), the column moves the next step of size dt would make. */
+typedef struct boltz_fks_s* boltz_fks;
+boltz_status boltz_fks_create(boltz_grid g, int64_t n_x, double dx, boltz_fks* out);
+boltz_status boltz_fks_step(boltz_fks s, const boltz_batch* b, const void* f_in, void* f_out,
+                            const void* inflow_lo, const void* inflow_hi, double dt, double tau,
+                            void* stream);
+boltz_status boltz_fks_time(boltz_fks s, double* t);
+boltz_status boltz_fks_set_time(boltz_fks s, double t);
+boltz_status boltz_fks_shifts(boltz_fks s, double dt, int* d);
+boltz_status boltz_fks_destroy(boltz_fks s);
 
 /* U[c] = (rho, rho u, E) of every cell (Eq. i5 on the grid, Eq. DM), float64,
  * U a device array of n_cells * 5 doubles.  Errors: EINVAL, ECUDA. */

@@ -19,6 +19,9 @@ solving the Boltzmann equation in multidimensions", arxiv 1608.08009):
 * ``plane``     -- the two-dimensional operator for Maxwell molecules (Sec. 3.3,
                    dimension two; Eq. dfor0) with its projection, relaxation and the 2D
                    BKW solution of Test 1.1 (Sec. 5).
+* ``fks``       -- the Fast Kinetic Scheme in one space dimension (Sec. 3.1): exact
+                   transport of the piecewise-constant distribution sampled at the cell
+                   centres, coupled to the collision step, with Dirichlet boundary states.
 * ``exact``     -- closed forms and independent quadratures used as pins: the exact
                    Carleman kernel at l=0, the classical kernel (Eq. KM) reduced to a
                    1D integral, the hard-sphere collision frequency of a Maxwellian,
@@ -28,8 +31,8 @@ solving the Boltzmann equation in multidimensions", arxiv 1608.08009):
 Everything is float64 numpy; library primitives (numpy FFT, scipy Bessel functions,
 numpy Gauss-Legendre nodes, numpy linear solves) serve as steps.  Functions with no
 independent pin say "parity unpinned" in their docstring; at present every exported
-function has at least one pin in ``tests/test_oracle_pins.py`` or
-``tests/test_oracle_plane.py`` (the latter against the error magnitudes printed in the
+function has at least one pin in ``tests/test_oracle_pins.py``,
+``tests/test_oracle_fks.py`` or ``tests/test_oracle_plane.py`` (the latter against the error magnitudes printed in the
 paper's Table test1, stored in ``tests/golden/``).
 """
 
@@ -53,4 +56,5 @@ from .operator import (  # noqa: F401
     constraint_matrix,
 )
 from . import exact  # noqa: F401
+from . import fks  # noqa: F401
 from . import plane  # noqa: F401

@@ -38,7 +38,8 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_server_step", "boltz_server_poll", "boltz_server_destroy", "boltz_relax_host",
             "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
             "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_host_chunks",
-            "boltz_server_submit_batch", "boltz_server_stats_get")
+            "boltz_server_submit_batch", "boltz_server_stats_get", "boltz_fks_create", "boltz_fks_step",
+            "boltz_fks_time", "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy")
 
 
 class BoltzError(RuntimeError):
@@ -106,6 +107,12 @@ def lib() -> ctypes.CDLL:
         L.boltz_server_submit.argtypes = [vp, i32, vp, vp, i32, P(i64)]
         L.boltz_server_submit_batch.argtypes = [vp, i32, vp, vp, i64, i32, P(i64)]
         L.boltz_server_stats_get.argtypes = [vp, P(boltz_server_stats)]
+        L.boltz_fks_create.argtypes = [vp, i64, f64, P(vp)]
+        L.boltz_fks_step.argtypes = [vp, P(boltz_batch), vp, vp, vp, vp, f64, f64, vp]
+        L.boltz_fks_time.argtypes = [vp, P(f64)]
+        L.boltz_fks_set_time.argtypes = [vp, f64]
+        L.boltz_fks_shifts.argtypes = [vp, f64, P(i32)]
+        L.boltz_fks_destroy.argtypes = [vp]
         L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
         L.boltz_server_pump.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.boltz_server_checkpoint.argtypes = [vp, i64, vp, P(i32)]
@@ -125,7 +132,8 @@ def lib() -> ctypes.CDLL:
                      "boltz_server_destroy", "boltz_relax_host", "boltz_plan_create", "boltz_plan_run",
                      "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump",
                      "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_server_submit_batch",
-                     "boltz_server_stats_get"):
+                     "boltz_server_stats_get", "boltz_fks_create", "boltz_fks_step", "boltz_fks_time",
+                     "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -311,6 +319,54 @@ class Server:
             boltz_destroy_server = lib().boltz_server_destroy
             _check(boltz_destroy_server(self.handle))
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Fks:
+    """Fast Kinetic Scheme in one space dimension (boltz_fks_*): rows of n_x cells of
+    width dx on `grid`; step() transports and collides f_in into f_out."""
+
+    def __init__(self, grid, n_x: int, dx: float):
+        h = ctypes.c_void_p()
+        _check(lib().boltz_fks_create(grid.handle, n_x, dx, ctypes.byref(h)))
+        self.handle = h.value
+        self.grid = grid
+
+    def step(self, batch: boltz_batch, f_in, f_out, inflow_lo, inflow_hi, dt: float, tau: float,
+             stream=None) -> None:
+        _check(lib().boltz_fks_step(self.handle, ctypes.byref(batch), _ptr(f_in), _ptr(f_out), _ptr(inflow_lo),
+                                    _ptr(inflow_hi), dt, tau, _stream(stream)))
+
+    @property
+    def time(self) -> float:
+        t = ctypes.c_double()
+        _check(lib().boltz_fks_time(self.handle, ctypes.byref(t)))
+        return t.value
+
+    @time.setter
+    def time(self, t: float) -> None:
+        _check(lib().boltz_fks_set_time(self.handle, t))
+
+    def shifts(self, dt: float):
+        d = (ctypes.c_int * self.grid.info["N"])()
+        _check(lib().boltz_fks_shifts(self.handle, dt, d))
+        return list(d)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _check(lib().boltz_fks_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:

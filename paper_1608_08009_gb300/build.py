@@ -22,7 +22,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libboltz.so")
-SOURCES = ["collide_f32.cu", "collide_f64.cu", "collide_tc.cu", "collide_2d.cu", "collide.cu", "api.cpp", "tables.cpp", "noalloc.cu", "serve.cpp", "host_io.cpp", "plan.cpp"]
+SOURCES = ["collide_f32.cu", "collide_f64.cu", "collide_tc.cu", "collide_2d.cu", "collide.cu", "api.cpp", "tables.cpp", "noalloc.cu", "serve.cpp", "host_io.cpp", "plan.cpp", "fks.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

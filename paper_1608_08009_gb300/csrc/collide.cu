@@ -286,7 +286,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                             const void* f_base, void* out, double a, double b, double s, double* Utgt,
                             int compute_targets, int project, cudaStream_t stream, const int64_t* cell_idx,
                             int64_t pool_cells, int groups, int cluster, const int64_t* split_idx,
-                            void* split_base) {
+                            void* split_base, const TransportArgs* tr) {
   if (n_cells == 0) return BOLTZ_OK;
   if (!collide_supported_grid(g, prec)) {
     set_error("unsupported (N, precision) combination");
@@ -308,6 +308,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
     a2.cell_idx = cell_idx;
     a2.pool_cells = pool_cells;
     a2.groups = 1;
+    if (tr) a2.tr = *tr;
     a2.geom.L = g->L;
     a2.geom.dv = g->dv;
     for (int i = 0; i < 25; ++i) a2.geom.G[i] = g->proj.G[i];
@@ -346,6 +347,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   args.geom.dv = g->dv;
   for (int i = 0; i < 25; ++i) args.geom.G[i] = g->proj.G[i];
   args.groups = G;
+  if (tr) args.tr = *tr;
   args.split_idx = nullptr;
   args.split_unit = 0;
   if (G > 1 && split_idx) {

@@ -64,11 +64,12 @@ constexpr unsigned kStatusTimeout = 8u;  // a bounded wait on an mbarrier gave u
 // the requested columns, and a CTA that waits there while cluster peers on other SMs wait
 // for it (at a cluster barrier, holding their own columns) could close a cycle with the
 // CTAs of another kernel running on another stream.  So no allocation may ever wait:
-// every kernel that shares its SM takes exactly kTmemShare columns (one size, so the 512
-// columns never fragment) and enough shared memory that at most 8 such CTAs fit on an SM
-// (8 x 64 = 512 columns); a kernel that needs more columns takes enough shared memory
-// that no such CTA fits beside it.  tmem_launch_smem (host side, below) sizes both from
-// the device's own shared-memory attributes.
+// every kernel that shares its SM allocates in shares of exactly kTmemShare columns (one
+// size, so the 512 columns never fragment; a CTA may hold a few) and takes enough shared
+// memory per share that at most 8 shares fit on an SM (8 x 64 = 512 columns); a kernel
+// that needs one larger allocation takes enough shared memory that no share fits beside
+// it.  tmem_launch_smem (host side, below) sizes both from the device's own
+// shared-memory attributes.
 constexpr int kTmemShare = 64;
 
 // Tensor-core transform modes of the float32 path (0: register FFT).
@@ -84,10 +85,11 @@ struct CollideCfg {
   // shared memory): sixteen warps per SM hide the table loads and barrier waits.  On
   // GB300: 2 CTAs (252 registers) 131k, 3 CTAs (168 registers, double buffer) 147k,
   // 4 CTAs 161k cell-collisions/s.
-  static constexpr bool kQuad = (sizeof(T) == 4 && N == 32 && C == 8 && TC == kTcNone);
+  // The same single-buffer layout serves C = 4: 256-thread CTAs, two per SM.
+  static constexpr bool kQuad = (sizeof(T) == 4 && N == 32 && (C == 8 || C == 4) && TC == kTcNone);
   static constexpr int MIN_BLOCKS = (TC == kTcTF32 || TC == kTc3xBF16) ? 2
                                     : (TC == kTc3xTF32)                  ? 1
-                                    : kQuad                              ? 4
+                                    : kQuad                              ? C / 2
                                                                          : 1;
   using T2 = typename Vec2<T>::type;
   static constexpr bool kF32 = sizeof(T) == 4;
@@ -104,6 +106,11 @@ struct CollideCfg {
   static constexpr bool kTmemSpec = kF32 && TC == kTcNone && N % 16 == 0;
   static constexpr int TMEM_NEED = ((THREADS / 32 + 3) / 4) * 2 * N;
   static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
+  // The spectrum's columns as kTmemShare-column allocations: one when they fit in one,
+  // otherwise one per group of four warps (2N <= 64 columns each).
+  static constexpr int TMEM_SHARES = !kTmemSpec ? 0 : TMEM_NEED <= kTmemShare ? 1 : (THREADS / 32 + 3) / 4;
+  static_assert(!kTmemSpec || TMEM_SHARES <= 4, "spectrum shares per CTA");
+  static_assert(!kTmemSpec || TMEM_SHARES == 1 || 2 * N <= kTmemShare, "one share per warp group");
   // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
   // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
   // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
@@ -118,27 +125,30 @@ struct CollideCfg {
   static constexpr size_t OFF_XB = FH * sizeof(T2);
   static constexpr size_t OFF_RED = OFF_XB + NXB * XB * sizeof(T2);
   // red: [WARPS][5] warp partials, then [5] Phi g and [5] Phi f_in of this CTA; then
-  // the last-arrival flag of split launches
+  // the last-arrival flag of split launches, room for four scatter mbarriers and four
+  // TMEM addresses (the spectrum's allocations)
   static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
+  static constexpr size_t OFF_MBAR = OFF_FLAG + 16;
+  static constexpr size_t OFF_TSLOT = OFF_MBAR + 32;
   // tensor-core transforms: operand tiles (rows of 2N floats, K-major without swizzle:
   // 8-row x 16-byte core matrices, K-adjacent ones 128 bytes apart), the DFT matrix,
   // the MMA-completion barrier and the TMEM address
   static constexpr int TC_K = 2 * N;
   static constexpr int TC_SPLIT = (TC == kTc3xTF32 || TC == kTc3xBF16) ? 2 : 1;
   static constexpr int TC_ES = (TC == kTc3xBF16) ? 2 : 4;  // operand element bytes
-  static constexpr size_t OFF_TCA = (OFF_FLAG + 16 + 1023) / 1024 * 1024;
+  static constexpr size_t OFF_TCA = (OFF_TSLOT + 16 + 1023) / 1024 * 1024;
   static constexpr size_t TCA_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * THREADS * TC_K * TC_ES : 0;
   static constexpr size_t OFF_TCW = OFF_TCA + TCA_BYTES;
   static constexpr size_t TCW_BYTES = (TC != kTcNone) ? (size_t)TC_SPLIT * TC_K * TC_K * TC_ES : 0;
   static constexpr size_t OFF_TCB = OFF_TCW + TCW_BYTES;  // mbarrier (8 B) + TMEM address (4 B)
-  // 32^3 4-CTA configuration: the kx-pass scatter uses st.async, which signals the
-  // owner's mbarrier (at OFF_FLAG + 16) with the bytes it delivers
+  // 32^3 single-buffer configurations: the kx-pass scatter uses st.async, which signals
+  // the owner's mbarrier (at OFF_MBAR) with the bytes it delivers
   static constexpr bool kAsyncScatter = kQuad && C > 1;
   static constexpr uint32_t SCATTER_BYTES = (uint32_t)NP * N * N * 2 * sizeof(T);  // received per term
-  static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_FLAG + 24;
+  static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_TSLOT + 16;
   // TMEM columns held: the spectrum pencils, or the tensor-core accumulator (2N <= 64)
   static constexpr int TC_TMEM_COLS = kTmemShare;
-  static constexpr int TMEM_HELD = kTmemSpec ? TMEM_COLS : (TC != kTcNone) ? TC_TMEM_COLS : 0;
+  static constexpr int TMEM_HELD = kTmemSpec ? TMEM_SHARES * kTmemShare : (TC != kTcNone) ? TC_TMEM_COLS : 0;
   static_assert(TC == kTcNone || (kF32 && THREADS == 128), "tensor-core transforms: float32, 128 pencils per CTA");
   static_assert(TC == kTcNone || 2 * N <= TC_TMEM_COLS, "tensor-core accumulator fits its columns");
   static_assert(THREADS % 32 == 0, "whole warps");
@@ -266,6 +276,19 @@ __device__ __forceinline__ void ld_local_chunk(const float2* p, float* re, float
 __device__ __forceinline__ void ld_local_chunk(const double2* p, double* re, double* im) {
   const double2 v = *p;
   re[0] = v.x; im[0] = v.y;
+}
+
+// Values of launch cell `cell` that the thread of velocity-x index x loads: the cell
+// itself, or with the transport stage fused in (CollideArgs::tr) the cell the shifted
+// interval comes from, or the boundary state beyond the row's end.
+template <typename TIO>
+__device__ __forceinline__ const TIO* cell_input(const CollideArgs& a, long long cell, int x, long long n) {
+  if (a.tr.nx <= 0) return reinterpret_cast<const TIO*>(a.f_in) + cell * n;
+  const long long row = cell / a.tr.nx, j = cell % a.tr.nx;
+  const long long src = j - ((long long)((a.tr.shift_pos >> x) & 1ull) - (long long)((a.tr.shift_neg >> x) & 1ull));
+  if (src < 0) return reinterpret_cast<const TIO*>(a.tr.inflow_lo) + row * n;
+  if (src >= a.tr.nx) return reinterpret_cast<const TIO*>(a.tr.inflow_hi) + row * n;
+  return reinterpret_cast<const TIO*>(a.f_in) + (row * a.tr.nx + src) * n;
 }
 
 // Term-group scratch of launch cell lc: partial gains [G][n], loss multipliers [n] and
@@ -582,29 +605,34 @@ collide_kernel(const CollideArgs args) {
   // lanes ordered (xl % VEC, ky or z), xl / VEC slowest
   const int xlt = (t / (VEC * N)) * VEC + t % VEC, grp = (t / VEC) % N;
   const int zt = grp;
-  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
   const T2* tab = reinterpret_cast<const T2*>(args.tab);
   const int M_eff = args.M_eff;
   const int ky_own = rank * NP + kyl;  // spectral ky of this thread's pencils
   const int x_own = rank * NP + xlt;   // physical x of this thread's rows
+  const TIO* fin = cell_input<TIO>(args, cell, x_own, n);
 
   T re[N], im[N];
   constexpr bool kTmemSpec = Cfg::kTmemSpec;
   constexpr bool kRegArr = kRegSpec && !kTmemSpec;
   T fr[kRegArr ? N : 1], fi[kRegArr ? N : 1];  // spectrum pencil in registers (tensor-core modes)
-  uint32_t spec_addr = 0, spec_tmem = 0;          // spectrum pencil in TMEM (register-FFT float32)
+  uint32_t spec_addr = 0;  // spectrum pencil in TMEM (register-FFT float32)
+  uint32_t* spec_slots = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TSLOT);
   if constexpr (kTmemSpec) {
-    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_FLAG + 8);
+    // one allocation of TMEM_COLS, or one kTmemShare-column share per group of four warps
     if ((threadIdx.x >> 5) == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                   "r"(Cfg::TMEM_COLS));
+#pragma unroll
+      for (int k = 0; k < Cfg::TMEM_SHARES; ++k)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(spec_slots + k)),
+                     "r"(Cfg::TMEM_SHARES == 1 ? Cfg::TMEM_COLS : kTmemShare));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    spec_tmem = *slot;
-    spec_addr = spec_tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + (uint32_t)((threadIdx.x >> 7) * 2 * N);
+    const int grp4 = threadIdx.x >> 7;  // group of four warps: lanes 0..127 of a column group
+    spec_addr = (Cfg::TMEM_SHARES == 1 ? spec_slots[0] + (uint32_t)(grp4 * 2 * N) : spec_slots[grp4]) +
+                ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
   }
 
   // tensor-core transforms: TMEM accumulator (2N columns), completion barrier, DFT matrix
@@ -637,7 +665,7 @@ collide_kernel(const CollideArgs args) {
   // for term i (before the arrive of term i), so no bytes of a term can arrive before
   // their phase is armed
   constexpr bool kAsync = Cfg::kAsyncScatter;
-  const uint32_t scat_mbar = smem_u32(smem_raw + Cfg::OFF_FLAG + 16);
+  const uint32_t scat_mbar = smem_u32(smem_raw + Cfg::OFF_MBAR);
   uint32_t scat_phase = 0;
   if constexpr (kAsync) {
     if (threadIdx.x == 0) {
@@ -822,10 +850,11 @@ collide_kernel(const CollideArgs args) {
     for (int z = 0; z < N; ++z) col[z * VEC] = mk2<T>(re[z], im[z]);
   };
   // pass along ky: thread (xl, z); outputs along y.  accumulate: Q+ += w Re Im; otherwise
-  // re[] keeps the loss multiplier L(v) along y.  release: these loads are this CTA's
+  // re[] keeps the loss multiplier L(v) along y.  release: these loads were this CTA's
   // last reads of its x-plane buffer for the term, so the write-after-read arrive (a
-  // release, which orders them before the peers' next stores) follows them directly and
-  // the transform runs after it.
+  // release, which orders them before the peers' next stores) ends the pass.  (Placed
+  // right after the loads instead, it measured slower: the release then also waits for
+  // the loads and for the term's scatter stores still in flight.)
   auto pass_ky = [&](const T2* XB, T wj, bool accumulate, bool release) {
     const T2* col = XB + Cfg::elem(xlt, 0, zt);
 #pragma unroll
@@ -834,13 +863,13 @@ collide_kernel(const CollideArgs args) {
       re[ky] = v.x;
       im[ky] = v.y;
     }
-    if constexpr (Cfg::NXB == 1 && C > 1) {
-      if (release) cluster_arrive_war<C>();
-    }
     inverse_1d();
     if (accumulate) {
 #pragma unroll
       for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
+    }
+    if constexpr (Cfg::NXB == 1 && C > 1) {
+      if (release) cluster_arrive_war<C>();
     }
   };
 
@@ -892,7 +921,8 @@ collide_kernel(const CollideArgs args) {
       pass_kz(XB0);
       __syncthreads();
       // single buffer: the owners' last reads of term i (the ky loads) come before the
-      // arrive that lets the peers scatter term i + 1 (their wait is in pass_kx)
+      // arrive (end of pass_ky) that lets the peers scatter term i + 1 (their wait is in
+      // pass_kx)
       pass_ky(XB0, wj, j < M_eff, more && kSplitWar);
       if constexpr (!kSplitWar) {
         if (more) cluster_barrier_war<C>();
@@ -907,8 +937,12 @@ collide_kernel(const CollideArgs args) {
     // the spectrum is no longer needed: free its TMEM columns
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(spec_tmem), "r"(Cfg::TMEM_COLS));
+    if ((threadIdx.x >> 5) == 0) {
+#pragma unroll
+      for (int k = 0; k < Cfg::TMEM_SHARES; ++k)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(spec_slots[k]),
+                     "r"(Cfg::TMEM_SHARES == 1 ? Cfg::TMEM_COLS : kTmemShare));
+    }
   }
   if constexpr (TC != kTcNone) {
     // every thread has read its last accumulator row: free the TMEM columns
@@ -1064,11 +1098,11 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   const int kyl = t / N, kzt = t % N;
   const int xlt = (t / (VEC * N)) * VEC + t % VEC, grp = (t / VEC) % N;
   const int zt = grp;
-  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
   const T2* tab = reinterpret_cast<const T2*>(args.tab);
   const int M_eff = args.M_eff;
   const int ky_own = rank * NP + kyl;
   const int x_own = rank * NP + xlt;
+  const TIO* fin = cell_input<TIO>(args, cell, x_own, n);
   // this thread's spectrum pencil (its (ky, kz), all kx) in TMEM, written once by the
   // forward x pass and read back in every kx pass
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_FLAG + 8);
@@ -1364,7 +1398,7 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
     writable = writable && ok;
     cell = ok ? s : 0;
   }
-  const TIO* fin = reinterpret_cast<const TIO*>(args.f_in) + cell * n;
+  const TIO* fin = cell_input<TIO>(args, cell, t, n);  // thread t: velocity-x index t
   const T2* tab = reinterpret_cast<const T2*>(args.tab);
   const int M_eff = args.M_eff;
   const double L = args.geom.L, dv = args.geom.dv;
@@ -1520,11 +1554,13 @@ static inline boltz_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 // Dynamic shared memory to launch a kernel with that holds `held` TMEM columns per CTA
-// (0: none; kTmemShare: shares the SM; more: must not share it with a TMEM holder), given
+// in `shares` allocations of kTmemShare columns (held = 0: none; held above shares x
+// kTmemShare: one larger allocation that must not share the SM with a TMEM holder), given
 // the `smem` bytes it uses.  With P bytes of shared memory per SM and r bytes kept by the
-// hardware per CTA, a sharing CTA takes at least P/9 - r + 1 bytes, so nine never fit; a
-// CTA holding more takes enough that not even one sharing CTA fits beside it.
-static inline boltz_status tmem_launch_smem(int held, size_t smem, int dev, size_t* out) {
+// hardware per CTA, a CTA of k shares takes at least k (P/9 + 1) - r bytes, so no nine
+// shares ever fit; a CTA holding a larger allocation takes enough that not even one
+// sharing CTA fits beside it.
+static inline boltz_status tmem_launch_smem(int held, size_t smem, int dev, size_t* out, int shares = 1) {
   *out = smem;
   if (held == 0) return BOLTZ_OK;
   int per_sm = 0, reserved = 0, optin = 0;
@@ -1535,8 +1571,9 @@ static inline boltz_status tmem_launch_smem(int held, size_t smem, int dev, size
     return cuda_fail(e, "shared memory attributes");
   const size_t P = (size_t)per_sm, r = (size_t)reserved;
   const size_t share = P / 9 + 1 - (r < P / 9 + 1 ? r : P / 9);
-  size_t need = share;
-  if (held > kTmemShare) need = P + 1 - share - 2 * r;  // (need + r) + (share + r) > P
+  // a CTA holding k shares takes (need + r) >= k (P / 9 + 1): at most 8 shares per SM
+  size_t need = shares * (P / 9 + 1) > r ? shares * (P / 9 + 1) - r : share;
+  if (held > shares * kTmemShare) need = P + 1 - share - 2 * r;  // (need + r) + (share + r) > P
   if (need > *out) *out = need;
   if (*out > (size_t)optin) {
     set_error("shared memory reservation for tensor memory exceeds the per-block limit");
@@ -1563,7 +1600,8 @@ static boltz_status launch_impl(const CollideArgs& a, int64_t n_cells, cudaStrea
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const unsigned long long bit = 1ull << (dev & 63);
   size_t smem = Cfg::SMEM;
-  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_HELD, Cfg::SMEM, dev, &smem);
+  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_HELD, Cfg::SMEM, dev, &smem,
+                                           Cfg::TMEM_SHARES > 1 ? Cfg::TMEM_SHARES : 1);
   if (ss != BOLTZ_OK) return ss;
   if (dev >= 64 || !(prepared[split].load(std::memory_order_acquire) & bit)) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

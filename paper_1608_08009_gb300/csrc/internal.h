@@ -25,6 +25,21 @@ struct KernelGeom {
   double G[25];
 };
 
+// Transport stage of the Fast Kinetic Scheme in one space dimension (Sec. 3.1, Eq. f_bar),
+// fused into the collision kernels' loads.  With nx > 0 the launch's cells are rows of nx
+// cells along x (cell c is cell j = c % nx of row c / nx) and the thread that handles
+// velocity-x index x reads cell j - d(x) of the same row, d(x) = +1 for the indices set in
+// shift_pos, -1 for those in shift_neg, 0 otherwise: the exact shift of the piecewise-
+// constant distribution sampled at the cell centres.  A source outside the row reads the
+// row's state beyond that end, inflow_lo[row] (j - d < 0) or inflow_hi[row] (j - d >= nx),
+// [rows][n] TIO each (the Dirichlet boundary states, or a neighbour's edge cells).
+struct TransportArgs {
+  int64_t nx;  // 0: no transport stage
+  uint64_t shift_pos, shift_neg;
+  const void* inflow_lo;
+  const void* inflow_hi;
+};
+
 // Argument block of every collision kernel (passed by value).
 struct CollideArgs {
   const void* f_in;    // [cells][N^3] TIO
@@ -55,6 +70,7 @@ struct CollideArgs {
   // unsigned arrival count (zero between launches); loss and arrivals are then unused.
   const int64_t* split_idx;
   size_t split_unit;
+  TransportArgs tr;
   KernelGeom geom;
 };
 
@@ -122,7 +138,8 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
                             double s, double* Utgt, int compute_targets, int project,
                             cudaStream_t stream, const int64_t* cell_idx = nullptr,
                             int64_t pool_cells = 0, int groups = -1, int cluster = 0,
-                            const int64_t* split_idx = nullptr, void* split_base = nullptr);
+                            const int64_t* split_idx = nullptr, void* split_base = nullptr,
+                            const TransportArgs* tr = nullptr);
 // Bytes of one term-group scratch block (CollideArgs::split_idx) of grid g with G groups:
 // a multiple of kSplitUnit.  split_idx entries passed to launch_collide count kSplitUnit
 // bytes from split_base.

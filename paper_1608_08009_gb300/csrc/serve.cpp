@@ -338,20 +338,24 @@ boltz_status boltz_server_submit(boltz_server s, int grid_index, const float* f_
 }  // extern "C"
 
 // Admission of queued jobs into the arena: every grid's queue in turn (round robin), each
-// first come first served while the head job's regions fit.
-static boltz_status admit(boltz_server_s* s) {
+// first come first served while the head job's regions fit.  Returns whether a queue head
+// is left waiting for memory.
+static boltz_status admit(boltz_server_s* s, bool* blocked) {
+  *blocked = false;
   cudaError_t e;
   const int ng = (int)s->pools.size();
   for (int k = 0; k < ng; ++k) {
     Pool& p = s->pools[(s->rr + k) % ng];
     while (!p.queue.empty()) {
       Job& j = s->jobs[p.queue.front()];
-      if (p.resident_cells + j.cells > p.cap) break;
       // one region: the distributions (aligned so that slot = offset / slot bytes), then
       // the scratch blocks
       const size_t fb = (size_t)j.cells * p.slot_bytes, sb = (size_t)j.cells * p.blk_bytes;
       size_t off = 0;
-      if (!s->alloc.alloc(fb + sb, p.slot_bytes, &off)) break;
+      if (p.resident_cells + j.cells > p.cap || !s->alloc.alloc(fb + sb, p.slot_bytes, &off)) {
+        *blocked = true;
+        break;
+      }
       j.off = off;
       j.bytes = fb + sb;
       s->used += j.bytes;
@@ -382,7 +386,16 @@ static boltz_status advance(boltz_server s, bool blocking, int* n_resident, int*
   cudaError_t e;
   boltz_status st = reap(s);
   if (st != BOLTZ_OK) return st;
-  if ((st = admit(s)) != BOLTZ_OK) return st;
+  bool blocked = false;
+  if ((st = admit(s, &blocked)) != BOLTZ_OK) return st;
+  if (blocking && blocked && !s->copying.empty()) {
+    // a queued job waits for memory that finished jobs return once their results have
+    // reached the host: wait for those copies, then admit again
+    for (int64_t id : s->copying)
+      if ((e = cudaEventSynchronize(s->jobs[id].done)) != cudaSuccess) return cuda_err(e, "job completion");
+    if ((st = reap(s)) != BOLTZ_OK) return st;
+    if ((st = admit(s, &blocked)) != BOLTZ_OK) return st;
+  }
   int issued = 0;
   for (auto& p : s->pools) {
     // iterations that have finished leave the ring
