@@ -64,6 +64,12 @@ WORKLOADS = {
     # eight angles (Test 1.1's grid), float32 transforms
     "plane32": dict(cells=262144, N=32, L=9.0, M=8, gamma=0.0, dt=0.02, prec="fp32_fft", f64=False, seed=20166,
                     dim=2, opts=dict(C_gamma=1.0 / (2.0 * math.pi))),
+    # Fast Kinetic Scheme, 1D x 3D Sod-like problem of Test 2.3 (N = 32 on [-16, 16)^3,
+    # M = 64, tau = 1e-2) on a fine mesh of 32768 cells per GPU over [0, 2] (x-slabs with
+    # ghost-cell exchange between GPUs); dt = 0.9 dx / max|v|; one fused transport +
+    # collision launch per step
+    "sod32": dict(cells=32768, N=32, L=16.0, M=64, gamma=1.0, dt=None, prec="fp32_fft", f64=False, seed=20169,
+                  fks=True, tau=1e-2),
     "bkw16": dict(cells=1, N=16, L=(3.0 + math.sqrt(2.0)) * 3.0, M=32, gamma=0.0, dt=0.01, prec="fp64", f64=True,
                   seed=20161, rk=2, init="bkw",
                   opts=dict(dirs_kind=1, C_gamma=1.0 / (4.0 * math.pi), radial_rank=16, term_groups=64)),
@@ -174,6 +180,31 @@ def shard_cells(rank: int, cells_per_rank: int) -> range:
     """Cells of the global seeded batch owned by `rank` (weak scaling: a fixed number per
     rank; cells are independent, so no data is exchanged between ranks)."""
     return range(rank * cells_per_rank, (rank + 1) * cells_per_rank)
+
+
+def fks_ghosts(f, lo_bc, hi_bc):
+    """Boundary states of this rank's x-slab for the next step of the Fast Kinetic Scheme
+    (Sec. 4.2, fig. mpi-decomp: the sub-domains' edge cells are exchanged after the
+    collision step): the left neighbour's last cell and the right neighbour's first cell,
+    or the domain's own boundary states at its ends.  The transport stage moves a column
+    by at most one cell per step, so one ghost cell per side is all a step reads.  f:
+    [cells][...] this rank's slab (CPU tensors over gloo, CUDA tensors over NCCL)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return lo_bc, hi_bc
+    rank, ws = dist.get_rank(), dist.get_world_size()
+    lo, hi, reqs = lo_bc, hi_bc, []
+    if rank > 0:
+        lo = torch.empty_like(f[:1])
+        reqs += [dist.irecv(lo, rank - 1), dist.isend(f[:1].contiguous(), rank - 1)]
+    if rank < ws - 1:
+        hi = torch.empty_like(f[-1:])
+        reqs += [dist.irecv(hi, rank + 1), dist.isend(f[-1:].contiguous(), rank + 1)]
+    for r in reqs:
+        r.wait()
+    return lo, hi
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -475,6 +506,133 @@ def run_ragged(args, wl):
     print(json.dumps(line), flush=True)
     for g in grids:
         g.close()
+    return 0
+
+
+def run_fks(args, wl):
+    """Fast Kinetic Scheme steps (boltz_fks_step: transport fused into the collision
+    launch) on the Sod-like data; x-slabs per rank with one ghost cell exchanged per side
+    and step (fks_ghosts, NCCL under torchrun).  value = cells of all ranks x steps / time;
+    the timed step includes the exchange."""
+    import torch
+
+    from paper_1608_08009_gb300 import boltz as B
+    from paper_1608_08009_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.lib()
+    N, L, M, cells, tau = wl["N"], wl["L"], wl["M"], wl["cells"], wl["tau"]
+    grid = B.Grid(N, L, wl["gamma"], M)
+    prec = {"fp64": B.BOLTZ_FP64, "fp32_fft": B.BOLTZ_FP32_FFT}[wl["prec"]]
+    dtype = torch.float64 if wl["f64"] else torch.float32
+    nx_all = cells * ws
+    dx = 2.0 / nx_all
+    dt = 0.9 * dx / L  # Eq. Time: |v_x| <= L on the grid
+    fl, fr = (torch.from_numpy(a).to(device="cuda", dtype=dtype) for a in W.sod_states(N, L))
+    xc = (torch.arange(rank * cells, (rank + 1) * cells, device="cuda", dtype=torch.float64) + 0.5) * dx
+    f0 = torch.where((xc <= 1.0)[:, None, None, None], fl[None], fr[None]).contiguous()
+    f, g2 = f0.clone(), torch.empty_like(f0)
+    lo_bc, hi_bc = fl[None].contiguous(), fr[None].contiguous()
+    batch = grid.batch(cells, prec, wl["f64"])
+    stream = torch.cuda.current_stream()
+    fks = B.Fks(grid, cells, dx)
+
+    def step(a, b):
+        lo, hi = fks_ghosts(a, lo_bc, hi_bc)
+        fks.step(batch, a, b, lo, hi, dt, tau, stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(f, g2)
+        f, g2 = g2, f
+    B.boltz_stream_status(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step(f, g2)
+        ev[k][1].record(stream)
+        f, g2 = g2, f
+    t1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    B.boltz_stream_status(stream)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), "cuda")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    value = cells * ws * args.steps / (total_ms / 1000.0)
+    # end to end: every step uploads the slab from pinned host memory, steps it and reads
+    # the result back
+    host = f.cpu().pin_memory()
+    out_host = torch.empty_like(host).pin_memory()
+    nbytes = host.numel() * host.element_size()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        f.copy_(host, non_blocking=True)
+        step(f, g2)
+        out_host.copy_(g2, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    B.boltz_stream_status(stream)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
+    if rank == 0:
+        flops_cell = algorithmic_flops(N, grid.info["M_eff"])
+        avg_s = statistics.mean(step_ms) / 1000.0
+        achieved = flops_cell * cells / avg_s / 1e12
+        peak = NOMINAL_FP32_TFLOPS if prec != B.BOLTZ_FP64 else NOMINAL_FP64_TFLOPS
+        rho = None
+        try:
+            Ub = torch.empty(cells, 5, dtype=torch.float64, device="cuda")
+            B.boltz_moments(batch, f, Ub, stream)
+            B.boltz_stream_status(stream)
+            rho = Ub[:, 0].cpu()
+        except Exception:
+            pass
+        line = {
+            "metric": "cell-collisions/s", "value": value, "unit": "cell-collisions/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == B.BOLTZ_FP64 else "f32", "data": "synthetic",
+            "config": {"workload": "sod32", "cells_per_gpu": cells, "cells_total": nx_all, "N_v": N, "L": L,
+                       "M_dirs": M, "gamma": wl["gamma"], "tau": tau, "dx": dx, "dt": dt,
+                       "domain": "[0, 2], Dirichlet states at both ends, x-slabs per GPU with one ghost cell",
+                       "precision": wl["prec"], "f_storage": "f64" if wl["f64"] else "f32",
+                       "l2_policy": "inputs larger than L2 (f is %.1f GB)" % (nbytes / 1e9),
+                       "parallelism": f"x-slabs, {ws} GPU(s), ghost exchange per step"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "algorithmic_bytes": 2 * nbytes,
+                         "kernel": "collide_kernel with the transport stage in its loads (one launch per step)",
+                         "flops_per_cell": flops_cell},
+            "e2e": {"value": cells * ws * e2e_steps / (e2e_ms / 1000.0), "unit": "cell-collisions/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "density_range_after": [float(rho.min()), float(rho.max())] if rho is not None else None,
+            "time_after": fks.time,
+        }
+        print(json.dumps(line), flush=True)
+    fks.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    grid.close()
     return 0
 
 
@@ -871,6 +1029,8 @@ def main():
         return run_reference(args, wl)
     if wl.get("ragged"):
         return run_ragged(args, wl)
+    if wl.get("fks"):
+        return run_fks(args, wl)
     return run_ours(args, wl)
 
 

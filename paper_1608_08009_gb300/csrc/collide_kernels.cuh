@@ -145,6 +145,7 @@ struct CollideCfg {
   // the owner's mbarrier (at OFF_MBAR) with the bytes it delivers
   static constexpr bool kAsyncScatter = kQuad && C > 1;
   static constexpr uint32_t SCATTER_BYTES = (uint32_t)NP * N * N * 2 * sizeof(T);  // received per term
+  static_assert(!kAsyncScatter || (NCH <= 4 && (THREADS / NCH) % 32 == 0), "per-chunk mbarriers and barriers");
   static constexpr size_t SMEM = (TC != kTcNone) ? OFF_TCB + 16 : OFF_TSLOT + 16;
   // TMEM columns held: the spectrum pencils, or the tensor-core accumulator (2N <= 64)
   static constexpr int TC_TMEM_COLS = kTmemShare;
@@ -659,19 +660,23 @@ collide_kernel(const CollideArgs args) {
     tc.tmem = *tmem_slot;
     tc.phase = 0u;
   }
-  // asynchronous scatter (32^3, 4 CTAs per SM): the owner's mbarrier counts the bytes
-  // that reach its x-plane buffer; it is armed for term 0 at initialisation (before this
-  // CTA's first write-after-read arrive) and re-armed for term i + 1 right after the wait
-  // for term i (before the arrive of term i), so no bytes of a term can arrive before
-  // their phase is armed
+  // asynchronous scatter (32^3 single-buffer layout): the owner has one mbarrier per
+  // chunk of its x-slab (chunk c: the x-planes c VEC .. c VEC + VEC - 1, whose kz and ky
+  // passes are done by threads [c THREADS / NCH, (c + 1) THREADS / NCH) alone), counting
+  // the bytes that reach that chunk of its buffer, so the warps of a chunk start as soon
+  // as their planes have landed.  Each is armed for term 0 at initialisation (before this
+  // CTA's first write-after-read arrive) and re-armed for term i + 1 by the chunk's first
+  // thread right after its wait for term i (before the arrive of term i), so no bytes of
+  // a term can arrive before their phase is armed
   constexpr bool kAsync = Cfg::kAsyncScatter;
   const uint32_t scat_mbar = smem_u32(smem_raw + Cfg::OFF_MBAR);
   uint32_t scat_phase = 0;
   if constexpr (kAsync) {
     if (threadIdx.x == 0) {
-      mbar_init(scat_mbar, 1);
+      for (int c = 0; c < Cfg::NCH; ++c) mbar_init(scat_mbar + 8 * c, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);  // term 0's phase, armed before any arrive
+      // term 0's phases, armed before any arrive
+      for (int c = 0; c < Cfg::NCH; ++c) mbar_expect_tx(scat_mbar + 8 * c, Cfg::SCATTER_BYTES / Cfg::NCH);
     }
   }
   // inverse 1D transform of this thread's pencil: register FFT or tensor-core DFT
@@ -826,7 +831,7 @@ collide_kernel(const CollideArgs args) {
 #pragma unroll
         for (int q = 0; q < C; ++q)
           st_async_chunk(cluster_addr(a, q), reinterpret_cast<const float*>(re) + q * NP + c * VEC,
-                         reinterpret_cast<const float*>(im) + q * NP + c * VEC, cluster_addr(scat_mbar, q));
+                         reinterpret_cast<const float*>(im) + q * NP + c * VEC, cluster_addr(scat_mbar + 8 * c, q));
       } else if constexpr (C > 1) {
         const uint32_t a = smem_u32(dst);
 #pragma unroll
@@ -909,17 +914,23 @@ collide_kernel(const CollideArgs args) {
       pass_kx(j, XB0);
       const bool more = (i < nt - 1);
       if constexpr (kAsync) {
-        // every producer's bytes of this term have landed in this CTA's buffer
-        if (!mbar_wait(scat_mbar, scat_phase)) atomicOr(&g_boltz_status, kStatusTimeout);
+        // every producer's bytes of this term have landed in this thread's chunk
+        const uint32_t my_mbar = scat_mbar + 8 * (xlt / VEC);
+        if (!mbar_wait(my_mbar, scat_phase)) atomicOr(&g_boltz_status, kStatusTimeout);
         scat_phase ^= 1u;
-        // arm the next term's phase now: its bytes cannot come before this CTA's
+        // arm the chunk's next phase now: its bytes cannot come before this CTA's
         // write-after-read arrive below
-        if (more && threadIdx.x == 0) mbar_expect_tx(scat_mbar, Cfg::SCATTER_BYTES);
+        if (more && (threadIdx.x % (Cfg::THREADS / Cfg::NCH)) == 0) mbar_expect_tx(my_mbar, Cfg::SCATTER_BYTES / Cfg::NCH);
       } else {
         cluster_barrier<C>();
       }
       pass_kz(XB0);
-      __syncthreads();
+      if constexpr (kAsync) {
+        // the chunk's own threads wrote its planes: a barrier among them (ids 1 ..)
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + xlt / VEC), "r"(Cfg::THREADS / Cfg::NCH) : "memory");
+      } else {
+        __syncthreads();
+      }
       // single buffer: the owners' last reads of term i (the ky loads) come before the
       // arrive (end of pass_ky) that lets the peers scatter term i + 1 (their wait is in
       // pass_kx)

@@ -13,6 +13,8 @@ Workloads (paper arxiv 1608.08009):
   * bkw -- the 3D BKW datum for Maxwell molecules at shape parameter K (rho = 1, T = 1).
   * two_maxwellians_2d -- the two-Maxwellian cells in two velocity dimensions (the 2D
     Maxwell-molecule grids of Sec. 3.3).
+  * sod_states -- the two equilibrium states of the Sod-like Riemann problem of Part 2 of
+    the numerics (rho = 1, u = 0, T = 2.5 left of the middle; 0.125, 0, 0.25 right).
 """
 
 from __future__ import annotations
@@ -33,6 +35,14 @@ def _maxwellian(v, rho, u, T):
     vz = v[None, None, :]
     d2 = (vx - u[0]) ** 2 + (vy - u[1]) ** 2 + (vz - u[2]) ** 2
     return rho * (2.0 * math.pi * T) ** -1.5 * np.exp(-d2 / (2.0 * T))
+
+
+def sod_states(N: int, L: float):
+    """(left, right) Maxwellians [N, N, N] of the Sod-like data of Part 2: rho = 1, u = 0,
+    T = 2.5 for x <= length / 2 and rho = 0.125, u = 0, T = 0.25 beyond."""
+    v = velocity_axis(N, L)
+    zero = (0.0, 0.0, 0.0)
+    return _maxwellian(v, 1.0, zero, 2.5), _maxwellian(v, 0.125, zero, 0.25)
 
 
 def two_maxwellian_params(n_cells: int, seed: int):
