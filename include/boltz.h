@@ -228,11 +228,17 @@ int64_t boltz_host_chunks(int64_t n_cells, int64_t cell_bytes, int64_t chunk_cel
  * specialised per N, so a step is one launch per group; the plan captures the whole step
  * loop as one CUDA graph in which every group is a concurrent branch, and
  * boltz_plan_run launches that graph on `stream`.
- * Autotuning (BOLTZ_PLAN_AUTOTUNE) times, for every group, each candidate (term groups,
- * cluster size) on a copy of the group's cells at plan creation and keeps the fastest;
- * without it a group uses its grid's term_groups and the default cluster size, and the
- * results equal boltz_relax's bit for bit.  BOLTZ_PLAN_SERIAL puts the groups one after
- * another on one branch (for comparison).
+ * Autotuning (BOLTZ_PLAN_AUTOTUNE) chooses each group's (term groups, cluster size) at
+ * plan creation on copies of the groups' cells: every candidate of a group is timed alone
+ * and the three fastest are kept; then, starting from the grids' own settings, the groups
+ * are visited slowest first and a kept candidate is adopted only if the whole concurrent
+ * step (all groups at once, as the graph runs them) gets faster by more than 1 %.  With
+ * BOLTZ_PLAN_TUNE_PRECISION as well, a float32 register-FFT group whose N has tensor-core
+ * transforms (16, 32) may also be switched to BOLTZ_3XTF32_DFT when that is faster (a
+ * float32-class precision with a different rounding).  Without autotuning a group uses
+ * its grid's term_groups and the default cluster size, and the results equal
+ * boltz_relax's bit for bit.  BOLTZ_PLAN_SERIAL puts the groups one after another on one
+ * branch (for comparison).
  * Ownership: the caller owns the grids and the device arrays f, which must stay valid and
  * in place for the plan's life; each group's grid must be distinct and must not be used
  * by other calls while the plan runs (its scratch is shared).  The plan owns its
@@ -248,7 +254,7 @@ typedef struct {
   void* f;           /* device array [n_cells][N^3], advanced in place by each run      */
 } boltz_group;
 
-enum { BOLTZ_PLAN_AUTOTUNE = 1, BOLTZ_PLAN_SERIAL = 2 };
+enum { BOLTZ_PLAN_AUTOTUNE = 1, BOLTZ_PLAN_SERIAL = 2, BOLTZ_PLAN_TUNE_PRECISION = 4 };
 
 boltz_status boltz_plan_create(const boltz_group* groups, int n_groups, double dt, int steps, int rk_order,
                                int flags, void* stream, boltz_plan* out);
@@ -257,6 +263,9 @@ boltz_status boltz_plan_run(boltz_plan p, void* stream);
 /* The launch configuration chosen for group `group`: term groups, cluster size and the
  * tuned duration of one launch in microseconds (0 when not tuned).  Outputs nullable. */
 boltz_status boltz_plan_group_info(boltz_plan p, int group, int* term_groups, int* cluster, double* tuned_us);
+/* The precision a group's launches use (its own, or BOLTZ_3XTF32_DFT when autotuning with
+ * BOLTZ_PLAN_TUNE_PRECISION chose the tensor-core transforms).  Errors: EINVAL. */
+boltz_status boltz_plan_group_precision(boltz_plan p, int group, int* prec);
 /* Synchronises the device, frees the plan.  NULL is a no-op. */
 boltz_status boltz_plan_destroy(boltz_plan p);
 

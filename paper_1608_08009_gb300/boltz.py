@@ -39,7 +39,8 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_plan_create", "boltz_plan_run", "boltz_plan_group_info", "boltz_plan_destroy",
             "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_host_chunks",
             "boltz_server_submit_batch", "boltz_server_stats_get", "boltz_fks_create", "boltz_fks_step",
-            "boltz_fks_time", "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy")
+            "boltz_fks_time", "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy",
+            "boltz_plan_group_precision")
 
 
 class BoltzError(RuntimeError):
@@ -72,6 +73,7 @@ class boltz_group(ctypes.Structure):
 
 BOLTZ_PLAN_AUTOTUNE = 1
 BOLTZ_PLAN_SERIAL = 2
+BOLTZ_PLAN_TUNE_PRECISION = 4
 
 _lib = None
 
@@ -113,6 +115,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_fks_set_time.argtypes = [vp, f64]
         L.boltz_fks_shifts.argtypes = [vp, f64, P(i32)]
         L.boltz_fks_destroy.argtypes = [vp]
+        L.boltz_plan_group_precision.argtypes = [vp, i32, P(i32)]
         L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
         L.boltz_server_pump.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.boltz_server_checkpoint.argtypes = [vp, i64, vp, P(i32)]
@@ -133,7 +136,7 @@ def lib() -> ctypes.CDLL:
                      "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump",
                      "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_server_submit_batch",
                      "boltz_server_stats_get", "boltz_fks_create", "boltz_fks_step", "boltz_fks_time",
-                     "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy"):
+                     "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy", "boltz_plan_group_precision"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -450,7 +453,9 @@ class Plan:
     def info(self, group: int) -> dict:
         G, C, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(lib().boltz_plan_group_info(self.handle, group, ctypes.byref(G), ctypes.byref(C), ctypes.byref(us)))
-        return {"term_groups": G.value, "cluster": C.value, "tuned_us": us.value}
+        pr = ctypes.c_int()
+        _check(lib().boltz_plan_group_precision(self.handle, group, ctypes.byref(pr)))
+        return {"term_groups": G.value, "cluster": C.value, "tuned_us": us.value, "prec": pr.value}
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -85,8 +85,9 @@ struct CollideCfg {
   // shared memory): sixteen warps per SM hide the table loads and barrier waits.  On
   // GB300: 2 CTAs (252 registers) 131k, 3 CTAs (168 registers, double buffer) 147k,
   // 4 CTAs 161k cell-collisions/s.
-  // The same single-buffer layout serves C = 4: 256-thread CTAs, two per SM.
-  static constexpr bool kQuad = (sizeof(T) == 4 && N == 32 && (C == 8 || C == 4) && TC == kTcNone);
+  // The same single-buffer layout serves C = 4 (256-thread CTAs, two per SM) and C = 16
+  // (64-thread CTAs, eight per SM).
+  static constexpr bool kQuad = (sizeof(T) == 4 && N == 32 && (C == 4 || C == 8 || C == 16) && TC == kTcNone);
   static constexpr int MIN_BLOCKS = (TC == kTcTF32 || TC == kTc3xBF16) ? 2
                                     : (TC == kTc3xTF32)                  ? 1
                                     : kQuad                              ? C / 2
@@ -874,7 +875,22 @@ collide_kernel(const CollideArgs args) {
       for (int y = 0; y < N; ++y) acc[y] += wj * (re[y] * im[y]);
     }
     if constexpr (Cfg::NXB == 1 && C > 1) {
-      if (release) cluster_arrive_war<C>();
+      if (release) {
+        if constexpr (kAsync) {
+          // the chunk's threads meet (its named barrier, which orders their loads before
+          // what its threads do next); the chunk's first warp then arrives with .release,
+          // cumulative over all those loads, and the other warps relaxed: one warp per
+          // chunk pays for the release instead of every thread
+          asm volatile("bar.sync %0, %1;" ::"r"(1 + xlt / VEC), "r"(Cfg::THREADS / Cfg::NCH) : "memory");
+          if (((threadIdx.x % (Cfg::THREADS / Cfg::NCH)) >> 5) == 0) {
+            cluster_arrive_war<C>();
+          } else {
+            asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+          }
+        } else {
+          cluster_arrive_war<C>();
+        }
+      }
     }
   };
 

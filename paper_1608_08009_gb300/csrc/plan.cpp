@@ -78,6 +78,7 @@ namespace {
 
 struct Cand {
   int G = 1, cluster = 0;
+  int prec = 0;    // the group's precision, or the tensor-core mode it may switch to
   float ms = 0.f;  // one launch of the group alone
 };
 
@@ -91,21 +92,25 @@ constexpr int kStepEvals = 48;    // whole-step timings at most
 constexpr float kGain = 0.99f;    // adopt a candidate only if the step gets 1 % faster
 
 boltz_status launch_candidate(const PlanGroup& g, const TuneCopies& c, const Cand& k, cudaStream_t s) {
-  return boltz::launch_collide(g.grid, g.n_cells, g.prec, g.f_is_fp64, c.fa, nullptr, c.qa, 0.0, 1.0, 1e-3, g.U0, 1,
+  return boltz::launch_collide(g.grid, g.n_cells, k.prec, g.f_is_fp64, c.fa, nullptr, c.qa, 0.0, 1.0, 1e-3, g.U0, 1,
                                1, s, nullptr, 0, k.G, k.cluster);
 }
 
-boltz_status time_alone(const PlanGroup& g, const TuneCopies& c, int sms, cudaStream_t s, cudaEvent_t e0,
-                        cudaEvent_t e1, std::vector<Cand>& out) {
+boltz_status time_alone(const PlanGroup& g, const TuneCopies& c, int sms, bool tune_prec, cudaStream_t s,
+                        cudaEvent_t e0, cudaEvent_t e1, std::vector<Cand>& out) {
   int cl[4];
-  const int ncl = boltz::cluster_choices(g.grid->N, g.prec, cl);
+  int ncl = boltz::cluster_choices(g.grid->N, g.prec, cl);
+  // the tensor-core mode of the same N: one more candidate (default cluster, one group)
+  const bool tc = tune_prec && g.prec == BOLTZ_FP32_FFT && boltz::collide_supported_grid(g.grid, BOLTZ_3XTF32_DFT);
   cudaError_t e = cudaSuccess;
-  for (int ci = 0; ci < ncl; ++ci) {
+  for (int ci = 0; ci < ncl + (tc ? 1 : 0); ++ci) {
+    const bool tc_cand = (ci == ncl);
     for (int G = 1; G <= std::min(16, g.grid->M_eff); G *= 2) {
-      if (G > 1 && g.n_cells * cl[ci] * (G / 2) >= 2 * (int64_t)sms) break;  // the GPU is already full
+      if (G > 1 && (tc_cand || g.n_cells * cl[ci] * (G / 2) >= 2 * (int64_t)sms)) break;  // the GPU is full
       Cand k;
       k.G = G;
-      k.cluster = cl[ci];
+      k.cluster = tc_cand ? 0 : cl[ci];
+      k.prec = tc_cand ? BOLTZ_3XTF32_DFT : g.prec;
       float best = 1e30f, ms = 0.f;
       boltz_status st = BOLTZ_OK;
       for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up (and sizes the split scratch)
@@ -177,6 +182,7 @@ boltz_status autotune(boltz_plan_s* p, cudaStream_t s) {
     PlanGroup& g = p->groups[i];
     pick[i].G = g.term_groups;
     pick[i].cluster = g.cluster;
+    pick[i].prec = g.prec;
     if (g.n_cells == 0) continue;
     const size_t bytes = (size_t)g.n_cells * boltz::cell_points(g.grid) * (g.f_is_fp64 ? 8 : 4);
     if (cudaMalloc(&copies[i].fa, bytes) != cudaSuccess || cudaMalloc(&copies[i].qa, bytes) != cudaSuccess) {
@@ -189,12 +195,14 @@ boltz_status autotune(boltz_plan_s* p, cudaStream_t s) {
       st = plan_fail(e, "autotune copy");
       goto done;
     }
-    if ((st = time_alone(g, copies[i], sms, s, e0, e1, cands[i])) != BOLTZ_OK) goto done;
+    if ((st = time_alone(g, copies[i], sms, (p->flags & BOLTZ_PLAN_TUNE_PRECISION) != 0, s, e0, e1, cands[i])) !=
+        BOLTZ_OK)
+      goto done;
     if (cands[i].size() > (size_t)kKeep) cands[i].resize(kKeep);
     // the time alone of the grid's own setting orders the refinement
     pick[i].ms = 1e30f;
     for (const Cand& k : cands[i])
-      if (k.G == pick[i].G && k.cluster == pick[i].cluster) pick[i].ms = k.ms;
+      if (k.G == pick[i].G && k.cluster == pick[i].cluster && k.prec == pick[i].prec) pick[i].ms = k.ms;
     if (pick[i].ms == 1e30f && !cands[i].empty()) pick[i].ms = cands[i].front().ms;
   }
   {
@@ -209,7 +217,7 @@ boltz_status autotune(boltz_plan_s* p, cudaStream_t s) {
     for (size_t i : order) {
       for (const Cand& k : cands[i]) {
         if (evals >= kStepEvals) break;
-        if (k.G == pick[i].G && k.cluster == pick[i].cluster) continue;
+        if (k.G == pick[i].G && k.cluster == pick[i].cluster && k.prec == pick[i].prec) continue;
         std::vector<Cand> trial = pick;
         trial[i] = k;
         float t = 0.f;
@@ -224,6 +232,7 @@ boltz_status autotune(boltz_plan_s* p, cudaStream_t s) {
     for (size_t i = 0; i < ng; ++i) {
       p->groups[i].term_groups = pick[i].G;
       p->groups[i].cluster = pick[i].cluster;
+      p->groups[i].prec = pick[i].prec;
       p->groups[i].tuned_us = pick[i].ms * 1000.0;
     }
     p->tuned_step_us = base * 1000.0;
@@ -251,7 +260,7 @@ boltz_status boltz_plan_create(const boltz_group* groups, int n_groups, double d
     return BOLTZ_EINVAL;
   }
   if (!(dt > 0) || !(dt < 1e300) || steps < 0 || (rk_order != 1 && rk_order != 2) ||
-      (flags & ~(BOLTZ_PLAN_AUTOTUNE | BOLTZ_PLAN_SERIAL))) {
+      (flags & ~(BOLTZ_PLAN_AUTOTUNE | BOLTZ_PLAN_SERIAL | BOLTZ_PLAN_TUNE_PRECISION))) {
     set_error("dt must be positive and finite, steps >= 0, rk_order 1 or 2, flags known");
     return BOLTZ_EINVAL;
   }
@@ -385,6 +394,15 @@ boltz_status boltz_plan_group_info(boltz_plan p, int group, int* term_groups, in
   if (term_groups) *term_groups = g.term_groups;
   if (cluster) *cluster = g.cluster;
   if (tuned_us) *tuned_us = g.tuned_us;
+  return BOLTZ_OK;
+}
+
+boltz_status boltz_plan_group_precision(boltz_plan p, int group, int* prec) {
+  if (!p || !prec || group < 0 || group >= (int)p->groups.size()) {
+    set_error("bad plan group");
+    return BOLTZ_EINVAL;
+  }
+  *prec = p->groups[group].prec;
   return BOLTZ_OK;
 }
 

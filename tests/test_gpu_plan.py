@@ -112,3 +112,31 @@ def test_plan_rejects_shared_grid_and_bad_args():
         assert ei.value.status == B.BOLTZ_EINVAL
         with pytest.raises(B.BoltzError):
             B.Plan([(g, f, B.BOLTZ_FP64)], -1.0, 1)
+
+
+def test_plan_precision_tuning_is_opt_in_and_float32_class():
+    """BOLTZ_PLAN_TUNE_PRECISION may move a float32 FFT group of N = 16 to the 3xTF32
+    tensor-core transforms; either way the result stays within twice the float32 bound of
+    the oracle (3xTF32 is float32-class), and without the flag the precision never
+    changes."""
+    N, L, M, cells, dt = 16, 6.0, 16, 64, 0.003
+    from paper_1608_08009_gb300 import workloads as W
+
+    f = torch.from_numpy(W.two_maxwellians(cells, N, L, seed=171)).float().cuda()
+    og = O.make_grid(N, L, M=M)
+    f0 = f.double().cpu().numpy()
+    ref = O.relax(f0, og, dt, 1)
+    Qp, Lo = O.operator.gain_loss(f0, og)
+    tol = 2 * 1.25 * EPS32 * math.log2(og.n) * np.linalg.norm(Qp) / np.linalg.norm(Qp - f0 * Lo) + 4 * EPS32 * \
+        np.linalg.norm(f0) / np.linalg.norm(ref - f0)
+    for flags, may_switch in ((B.BOLTZ_PLAN_AUTOTUNE, False),
+                              (B.BOLTZ_PLAN_AUTOTUNE | B.BOLTZ_PLAN_TUNE_PRECISION, True)):
+        with B.Grid(N, L, 1.0, M) as g:
+            w = f.clone()
+            with B.Plan([(g, w, B.BOLTZ_FP32_FFT)], dt, 1, 1, flags) as p:
+                p.run()
+                B.boltz_stream_status()
+                prec = p.info(0)["prec"]
+            assert prec == B.BOLTZ_FP32_FFT or (may_switch and prec == B.BOLTZ_3XTF32_DFT)
+            d = w.double().cpu().numpy() - f0
+            assert np.linalg.norm(d - (ref - f0)) / np.linalg.norm(ref - f0) <= tol, prec
