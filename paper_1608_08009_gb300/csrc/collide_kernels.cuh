@@ -1368,8 +1368,9 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
 
 // ------------------------------------------------------------------------------------
 // Two dimensions (Maxwell molecules; Sec. 3.3 dimension two, Eq. dfor0).  A cell is N
-// threads (one pencil each) of a CTA that holds several cells; the cell's spectrum and
-// one N x (N+1) plane buffer live in shared memory, the gain accumulator in registers.
+// threads (one pencil each) of a CTA that holds several cells; the cell's spectrum (in
+// TMEM for float32 at N = 16, 32, in shared memory otherwise) and one N x (N+1) plane
+// buffer in shared memory, the gain accumulator in registers.
 // Per term: kx pass with the coefficients (thread ky, tables [term][kx][ky] read
 // coalesced across the cell's threads), transposed store, ky pass (thread x) and
 // Q+ += w Re Im along y.  Projection on (1, v_x, v_y, |v|^2/2) in float64 (the 5-slot
@@ -1380,18 +1381,30 @@ struct PlaneCfg {
   using T2 = typename Vec2<T>::type;
   static constexpr int RW = N + 1;
   static constexpr size_t BUF = (size_t)N * RW;  // T2 per plane
-  static constexpr size_t CELL_SMEM = 2 * BUF * sizeof(T2) + (size_t)(N + 1) * 10 * sizeof(double);
+  // float32 at N = 16, 32: each thread's spectrum pencil (2N floats) lives in TMEM (warp w:
+  // lanes 32 (w % 4) .., column group w / 4), so a cell's shared memory is its plane
+  // buffer and reduction rows only and two 8-cell CTAs fit on an SM
+  static constexpr bool kTmemSpec = sizeof(T) == 4 && (N == 16 || N == 32);
+  static constexpr size_t CELL_SMEM = (kTmemSpec ? 1 : 2) * BUF * sizeof(T2) + (size_t)(N + 1) * 10 * sizeof(double);
   static constexpr int CPB_SMEM = (int)((200u * 1024u) / CELL_SMEM);
   static constexpr int CPB = (256 / N < CPB_SMEM) ? 256 / N : CPB_SMEM;  // cells per CTA
   static constexpr int THREADS = CPB * N;
-  static constexpr size_t SMEM = (size_t)CPB * CELL_SMEM;
+  static constexpr int MIN_BLOCKS = kTmemSpec ? 2 : 1;
+  static constexpr int TMEM_SHARES = kTmemSpec ? ((THREADS / 32 + 3) / 4 * 2 * N + kTmemShare - 1) / kTmemShare : 0;
+  static constexpr int GROUP_COLS = 2 * N;  // columns per group of four warps
+  static constexpr size_t OFF_TSLOT = (size_t)CPB * CELL_SMEM;  // TMEM addresses (up to 4)
+  static constexpr size_t SMEM = OFF_TSLOT + 16;
+  static_assert(!kTmemSpec || TMEM_SHARES <= 4, "spectrum shares per CTA");
+  static_assert(!kTmemSpec || TMEM_SHARES == 1 || GROUP_COLS == kTmemShare, "one share per warp group");
+  static_assert(OFF_TSLOT % 8 == 0, "aligned TMEM address slots");
   static_assert(CPB >= 1, "one cell must fit");
   static_assert(N <= 32 || CPB <= 15, "one named barrier per cell (ids 1..15)");
   static_assert((2 * BUF * sizeof(T2)) % 16 == 0 || true, "");
 };
 
 template <typename T, typename TIO, int N>
-__global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(const CollideArgs args, long long n_cells) {
+__global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS, PlaneCfg<T, N>::MIN_BLOCKS)
+collide2d_kernel(const CollideArgs args, long long n_cells) {
   using Cfg = PlaneCfg<T, N>;
   using T2 = typename Cfg::T2;
   constexpr int RW_ = Cfg::RW;
@@ -1408,10 +1421,30 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
       asm volatile("bar.sync %0, %1;" ::"r"(1 + ci), "r"(N) : "memory");
     }
   };
+  constexpr bool kTmemSpec = Cfg::kTmemSpec;
   unsigned char* base = smem_raw + (size_t)ci * Cfg::CELL_SMEM;
-  T2* Fh = reinterpret_cast<T2*>(base);                 // spectrum [kx][ky]
-  T2* P = Fh + Cfg::BUF;                                 // plane buffer [x][ky]
-  double* red = reinterpret_cast<double*>(P + Cfg::BUF); // [N][10], then [10] cell totals
+  T2* Fh = reinterpret_cast<T2*>(base);                  // spectrum [kx][ky] (not with TMEM)
+  T2* P = Fh + (kTmemSpec ? 0 : Cfg::BUF);                // plane buffer [x][ky]
+  double* red = reinterpret_cast<double*>(P + Cfg::BUF);  // [N][10], then [10] cell totals
+  uint32_t* spec_slots = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TSLOT);
+  uint32_t spec_addr = 0;
+  if constexpr (kTmemSpec) {
+    if ((threadIdx.x >> 5) == 0) {
+#pragma unroll
+      for (int k = 0; k < Cfg::TMEM_SHARES; ++k)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(spec_slots + k)),
+                     "r"(kTmemShare));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int grp4 = threadIdx.x >> 7;
+    const uint32_t lane_off = (uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16;
+    spec_addr = (Cfg::TMEM_SHARES == 1 ? spec_slots[0] + (uint32_t)(grp4 * Cfg::GROUP_COLS) : spec_slots[grp4]) +
+                lane_off;
+  }
 
   long long lc = (long long)blockIdx.x * Cfg::CPB + ci;
   const bool in_launch = lc < n_cells;  // the last CTA may hold fewer cells
@@ -1458,7 +1491,20 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
       const bool z0 = (kx == N / 2) || (t == N / 2);
-      Fh[kx * RW_ + t] = z0 ? mk2<T>(T(0), T(0)) : mk2<T>(re[kx] * scale, im[kx] * scale);
+      if constexpr (kTmemSpec) {
+        re[kx] = z0 ? T(0) : re[kx] * scale;
+        im[kx] = z0 ? T(0) : im[kx] * scale;
+      } else {
+        Fh[kx * RW_ + t] = z0 ? mk2<T>(T(0), T(0)) : mk2<T>(re[kx] * scale, im[kx] * scale);
+      }
+    }
+    if constexpr (kTmemSpec) {
+#pragma unroll
+      for (int c = 0; c < N; c += 16) {
+        tmem_st16(spec_addr + c, reinterpret_cast<const float*>(re) + c);
+        tmem_st16(spec_addr + N + c, reinterpret_cast<const float*>(im) + c);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
   }
 #pragma unroll
@@ -1468,9 +1514,22 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
   for (int j = 0; j <= M_eff; ++j) {
     const T wj = (j < M_eff) ? (T)args.w[j] : T(0);
     const T2* tj = tab + (size_t)j * n + t;
+    if constexpr (kTmemSpec) {
+#pragma unroll
+      for (int c = 0; c < N; c += 16) {
+        tmem_ld16(spec_addr + c, reinterpret_cast<float*>(re) + c);
+        tmem_ld16(spec_addr + N + c, reinterpret_cast<float*>(im) + c);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    }
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
-      const T2 c = Fh[kx * RW_ + t];
+      T2 c;
+      if constexpr (kTmemSpec) {
+        c = mk2<T>(re[kx], im[kx]);
+      } else {
+        c = Fh[kx * RW_ + t];
+      }
       const T2 ab = __ldg(tj + kx * N);
       re[kx] = ab.x * c.x - ab.y * c.y;
       im[kx] = ab.x * c.y + ab.y * c.x;
@@ -1493,6 +1552,16 @@ __global__ void __launch_bounds__(PlaneCfg<T, N>::THREADS) collide2d_kernel(cons
     cell_sync();  // the next term overwrites P
   }
   // re[] holds the loss multiplier L along y of row x = t
+  if constexpr (kTmemSpec) {
+    // the spectrum is no longer needed: free its TMEM columns
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+#pragma unroll
+      for (int k = 0; k < Cfg::TMEM_SHARES; ++k)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(spec_slots[k]), "r"(kTmemShare));
+    }
+  }
 
   const int x = t;
   const double vx = -L + x * dv;
@@ -1739,13 +1808,17 @@ static boltz_status launch2d_impl(const CollideArgs& a, int64_t n_cells, cudaStr
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const unsigned long long bit = 1ull << (dev & 63);
+  size_t smem = Cfg::SMEM;
+  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_SHARES * kTmemShare, Cfg::SMEM, dev, &smem,
+                                           Cfg::TMEM_SHARES > 1 ? Cfg::TMEM_SHARES : 1);
+  if (ss != BOLTZ_OK) return ss;
   if (dev >= 64 || !(prepared.load(std::memory_order_acquire) & bit)) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return cuda_fail(e, "cudaFuncSetAttribute");
     if (dev < 64) prepared.fetch_or(bit, std::memory_order_release);
   }
   const long long blocks = (n_cells + Cfg::CPB - 1) / Cfg::CPB;
-  kern<<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, st>>>(a, (long long)n_cells);
+  kern<<<(unsigned)blocks, Cfg::THREADS, smem, st>>>(a, (long long)n_cells);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "collide2d launch");
   return BOLTZ_OK;
 }
