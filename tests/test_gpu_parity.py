@@ -256,7 +256,7 @@ def test_full_size_mixed_sampled():
         B.boltz_collide(batch, fd, Q)
         B.boltz_stream_status()
         # whole batch against the float64 GPU path on the same (float32-rounded) input
-        num, den, worst = 0.0, 0.0, 0.0
+        num, den, per_cell = 0.0, 0.0, []
         for c0 in range(0, n_cells, 4096):
             f64 = fd[c0:c0 + 4096].double()
             Q64 = torch.empty_like(f64)
@@ -266,10 +266,17 @@ def test_full_size_mixed_sampled():
             r = Q64.flatten(1)
             num += float((d * d).sum())
             den += float((r * r).sum())
-            worst = max(worst, float((d.norm(dim=1) / r.norm(dim=1)).max()))
+            per_cell.append((d.norm(dim=1) / r.norm(dim=1)).cpu())
             del f64, Q64, d, r
         err_batch = math.sqrt(num / den)
-        print(f"32768 x 32^3 float32: batch rel L2 vs float64 {err_batch:.3e}, worst cell {worst:.3e}")
+        pc = torch.cat(per_cell).numpy()
+        # per cell the relative error scales with the cell's conditioning
+        # kappa_c = ||Q+_c|| / ||Q_c||: near-equilibrium cells (two close Maxwellians) have
+        # a tiny Q, so their relative error is large for any fixed precision; the target
+        # is the batch metric (relative L2 over all cells and velocities)
+        print(f"32768 x 32^3 float32: batch rel L2 vs float64 {err_batch:.3e}; per cell: median "
+              f"{np.median(pc):.2e}, 90 % {np.quantile(pc, 0.9):.2e}, 99 % {np.quantile(pc, 0.99):.2e}, max "
+              f"{pc.max():.2e}, above 1e-5: {(pc > 1e-5).mean() * 100:.1f} %")
         assert err_batch <= 1e-5
         # conservation on every cell: mass and energy of Q against those of |Q|
         U = torch.empty(n_cells, 5, dtype=torch.float64, device="cuda")
@@ -285,8 +292,13 @@ def test_full_size_mixed_sampled():
         Qref = O.collide(f_s, og)
         Qs = Q[sample].double().cpu().numpy()
         assert rel_l2(Qs, Qref) <= 1e-5
+        Qp_s, _ = O.operator.gain_loss(f_s, og)
         for k in range(len(sample)):
             assert rel_l2(Qs[k:k + 1], Qref[k:k + 1]) <= fp32_tol(f_s[k:k + 1], og) + EPS32, sample[k]
+            # conditioning-free: the error against the size of the gain, which both terms
+            # of Q = Q+ - f L carry, within the float32 transform bound itself
+            err_gain = np.linalg.norm(Qs[k] - Qref[k]) / np.linalg.norm(Qp_s[k])
+            assert err_gain <= 1.25 * EPS32 * math.log2(og.n), (sample[k], err_gain)
         # one Euler step of the relax launch the benchmark times: f + dt Q with the
         # projection targets of f itself, stored as float32
         B.boltz_relax(batch, fd, dt, 1, 1)
