@@ -1077,7 +1077,12 @@ struct LargeCfg {
   static constexpr size_t OFF_ACC = XB * sizeof(float2);
   static constexpr size_t OFF_RED = OFF_ACC + ACC * sizeof(float);
   static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
-  static constexpr size_t SMEM = OFF_FLAG + 16;  // flag, then the TMEM address
+  // flag, the TMEM address, then one scatter mbarrier per chunk of the x-slab
+  static constexpr size_t OFF_MBAR = OFF_FLAG + 16;
+  static constexpr size_t SMEM = OFF_MBAR + 8 * NCH;
+  // bytes a CTA receives per term (its x-slab of one term's kx-pass outputs)
+  static constexpr uint32_t SCATTER_BYTES = (uint32_t)NP * N * N * 2 * sizeof(float);
+  static_assert(NCH <= 4 && (THREADS / NCH) % 32 == 0, "per-chunk mbarriers and named barriers");
   // spectrum pencils in TMEM: warp w uses lanes 32 (w % 4) .. + 31 and the column group
   // w / 4 of 2N columns (N real parts, then N imaginary parts)
   static constexpr int TMEM_NEED = ((WARPS + 3) / 4) * 2 * N;
@@ -1143,6 +1148,20 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem_base = *tmem_slot;
   const uint32_t spec_addr = tmem_base + ((uint32_t)(32 * ((t >> 5) & 3)) << 16) + (uint32_t)((t >> 7) * 2 * N);
+  // Exchange per term as in collide_kernel's 32^3 single-buffer form: st.async scatter
+  // completing on one mbarrier per chunk of the owner's x-slab (chunk c: planes c VEC ..,
+  // whose kz and ky passes are done by threads [c THREADS / NCH, ...) alone), armed for
+  // term 0 here, before this CTA's first write-after-read arrive, and re-armed by the
+  // chunk's first thread right after its wait for each term.
+  const uint32_t scat_mbar = smem_u32(smem_raw + Cfg::OFF_MBAR);
+  uint32_t scat_phase = 0;
+  if (t == 0) {
+    for (int c = 0; c < NCH; ++c) mbar_init(scat_mbar + 8 * c, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int c = 0; c < NCH; ++c) mbar_expect_tx(scat_mbar + 8 * c, Cfg::SCATTER_BYTES / NCH);
+  }
+  const int chunk = xlt / VEC;  // this thread's chunk in the kz and ky passes
+  constexpr int CH_THREADS = Cfg::THREADS / NCH;
 
   T re[N], im[N];
   const double L = args.geom.L, dv = args.geom.dv;
@@ -1203,6 +1222,10 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
 #pragma unroll
       for (int q = 0; q < C; ++q) ld_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
     }
+    // the peers must be done gathering from this CTA's buffer before the first scatter
+    // into it: this arrive (a release, ordering the gathers) and the wait in the first kx
+    // pass, just before its stores
+    cluster_arrive_war<C>();
     fft_regs<N, -1>(re, im);
     const T scale = T(1) / T(n);
     const bool nyq = (ky_own == N / 2) || (kzt == N / 2);
@@ -1219,8 +1242,11 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
-  for (int i = t; i < (int)Cfg::ACC; i += Cfg::THREADS) accs[i] = 0.f;
-  cluster_barrier<C>();  // peers done gathering from this CTA's buffer
+  {  // this thread's row of the gain accumulator
+    float* a = accs + (size_t)xlt * N * N + zt;
+#pragma unroll
+    for (int y = 0; y < N; ++y) a[y * N] = 0.f;
+  }
 
   // ---- angular loop --------------------------------------------------------------------
   const int j0 = kSplit ? (int)(((long long)gi * M_eff) / G) : 0;
@@ -1246,14 +1272,23 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
         im[kx] = ab.x * cim + ab.y * cr;
       }
       fft_regs<N, +1>(re, im);
+      cluster_wait_war<C>();  // every owner has read its buffer
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         const uint32_t a = smem_u32(XB + Cfg::elem(c * VEC, ky_own, kzt));
 #pragma unroll
-        for (int q = 0; q < C; ++q) st_cluster_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC);
+        for (int q = 0; q < C; ++q)
+          st_async_chunk(cluster_addr(a, q), re + q * NP + c * VEC, im + q * NP + c * VEC,
+                         cluster_addr(scat_mbar + 8 * c, q));
       }
     }
-    cluster_barrier<C>();
+    const bool more = (i < nt - 1);
+    {  // every producer's bytes of this term have landed in this thread's chunk
+      const uint32_t my_mbar = scat_mbar + 8 * chunk;
+      if (!mbar_wait(my_mbar, scat_phase)) atomicOr(&g_boltz_status, kStatusTimeout);
+      scat_phase ^= 1u;
+      if (more && (t % CH_THREADS) == 0) mbar_expect_tx(my_mbar, Cfg::SCATTER_BYTES / NCH);
+    }
     {  // kz pass: thread (xl, ky)
       T2* col = XB + Cfg::elem(xlt, grp, 0);
 #pragma unroll
@@ -1266,7 +1301,8 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
 #pragma unroll
       for (int z = 0; z < N; ++z) col[z * VEC] = make_float2(re[z], im[z]);
     }
-    __syncthreads();
+    // the chunk's own threads wrote its planes: a barrier among them (ids 1 ..)
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + chunk), "r"(CH_THREADS) : "memory");
     {  // ky pass: thread (xl, z); Q+ += w Re Im into shared memory, or keep L in re[]
       const T2* col = XB + Cfg::elem(xlt, 0, zt);
 #pragma unroll
@@ -1282,8 +1318,19 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
         for (int y = 0; y < N; ++y) a[y * N] += wj * (re[y] * im[y]);
       }
     }
-    if (i < nt - 1) cluster_barrier_war<C>();  // owners done reading before the next scatter
+    if (more) {
+      // write-after-read: the chunk's threads meet (their loads of the term precede it),
+      // then the chunk's first warp arrives with .release (cumulative over them) and the
+      // others relaxed; the wait is in the next kx pass, before its stores
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + chunk), "r"(CH_THREADS) : "memory");
+      if (((t % CH_THREADS) >> 5) == 0) {
+        cluster_arrive_war<C>();
+      } else {
+        asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+      }
+    }
   }
+  if (nt == 0) cluster_wait_war<C>();  // a group without terms: close the forward arrive
 
   // the spectrum is no longer needed: free the TMEM columns
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
