@@ -57,7 +57,8 @@ WORKLOADS = {
     "mixed48": dict(cells=2048, N=48, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20167),
     "mixed64": dict(cells=512, N=64, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20168),
     # ragged batch: 10000 cells, N in {16: 40 %, 24: 30 %, 32: 25 %, 48: 5 %}, M in {32, 64},
-    # gamma in {0, 0.5, 1} drawn per cell; one group (grid) per (N, M, gamma)
+    # gamma in {0, 0.5, 1} drawn per cell, half the cells two-Maxwellian and half 3D BKW
+    # profiles; one group (grid) per (N, M, gamma)
     "ragged": dict(cells=10000, N=32, L=8.0, M=64, gamma=1.0, dt=0.0025, prec="fp32_fft", f64=False, seed=20164,
                    ragged=True),
     # 2D Maxwell molecules (Sec. 3.3 dimension two): 262144 cells of 32^2 on [-9, 9]^2,
@@ -406,15 +407,36 @@ RAGGED_L = {16: 6.0, 24: 7.0, 32: 8.0, 48: 8.0}
 
 def ragged_groups(wl: dict):
     """Seeded per-cell (N, M, gamma) of the ragged batch, grouped: {(N, M, gamma): cells}."""
+    return {k: len(v) for k, v in ragged_cells(wl).items()}
+
+
+def ragged_cells(wl: dict):
+    """Seeded per-cell draws of the ragged batch, grouped by (N, M, gamma): for each cell
+    of a group its initial datum, None for a two-Maxwellian cell, else the BKW shape
+    parameter K in U[0.6, 0.95] (half the cells each; K >= 3/5 keeps the 3D BKW profile
+    non-negative)."""
     rng = np.random.Generator(np.random.PCG64(wl["seed"]))
     n = wl["cells"]
     Ns = rng.choice([16, 24, 32, 48], size=n, p=[0.40, 0.30, 0.25, 0.05])
     Ms = rng.choice([32, 64], size=n)
     gs = rng.choice([0.0, 0.5, 1.0], size=n)
+    is_bkw = rng.random(n) < 0.5
+    Ks = rng.uniform(0.6, 0.95, size=n)
     groups = {}
-    for N, M, g in zip(Ns.tolist(), Ms.tolist(), gs.tolist()):
-        groups[(N, M, g)] = groups.get((N, M, g), 0) + 1
+    for N, M, g, b, K in zip(Ns.tolist(), Ms.tolist(), gs.tolist(), is_bkw.tolist(), Ks.tolist()):
+        groups.setdefault((N, M, g), []).append(K if b else None)
     return dict(sorted(groups.items()))
+
+
+def ragged_inputs(N: int, L: float, data: list, seed: int) -> np.ndarray:
+    """The cells of one ragged group: two-Maxwellian cells (seeded) and BKW profiles."""
+    from paper_1608_08009_gb300 import workloads as W
+
+    f = W.two_maxwellians(len(data), N, L, seed)
+    for c, K in enumerate(data):
+        if K is not None:
+            f[c] = W.bkw(N, L, K)
+    return f
 
 
 def run_ragged(args, wl):
@@ -425,21 +447,21 @@ def run_ragged(args, wl):
     import torch
 
     from paper_1608_08009_gb300 import boltz as B
-    from paper_1608_08009_gb300 import workloads as W
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     B.lib()
-    spec = ragged_groups(wl)
+    spec = ragged_cells(wl)
     grids, fs, f0s, info = [], [], [], []
-    for i, ((N, M, gamma), cells) in enumerate(spec.items()):
+    for i, ((N, M, gamma), data) in enumerate(spec.items()):
         L = RAGGED_L[N]
         g = B.Grid(N, L, gamma, M, C_gamma=1.0 / (4.0 * math.pi) if gamma == 0.0 else 1.0)
-        f = torch.from_numpy(W.two_maxwellians(cells, N, L, wl["seed"] + 1000 + i)).float().cuda()
+        f = torch.from_numpy(ragged_inputs(N, L, data, wl["seed"] + 1000 + i)).float().cuda()
         grids.append(g)
         fs.append(f)
         f0s.append(f.clone())
-        info.append({"N": N, "M": M, "gamma": gamma, "cells": cells, "M_eff": g.info["M_eff"]})
+        info.append({"N": N, "M": M, "gamma": gamma, "cells": len(data),
+                     "bkw_cells": sum(K is not None for K in data), "M_eff": g.info["M_eff"]})
     cells_total = sum(x["cells"] for x in info)
     flops = sum(algorithmic_flops(x["N"], x["M_eff"]) * x["cells"] for x in info)
     stream = torch.cuda.current_stream()
@@ -490,7 +512,8 @@ def run_ragged(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_tuned, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ragged", "cells": wl["cells"], "cells_run": cells_total,
-                   "mix": "N 16/24/32/48: 40/30/25/5 %; M 32/64; gamma 0/0.5/1 (rank-16 expansion for gamma != 1)",
+                   "mix": "N 16/24/32/48: 40/30/25/5 %; M 32/64; gamma 0/0.5/1 (rank-16 expansion for gamma != 1); "
+                          "data: half two-Maxwellian, half 3D BKW profiles with K in U[0.6, 0.95]",
                    "L_by_N": RAGGED_L, "dt": dt, "precision": "fp32_fft", "f_storage": "f32",
                    "l2_policy": "inputs larger than L2 (f is %.2f GB)" % (sum(f.numel() * 4 for f in fs) / 1e9),
                    "parallelism": "1 GPU"},

@@ -88,30 +88,40 @@ struct CollideCfg {
   // The same single-buffer layout serves C = 4 (256-thread CTAs, two per SM) and C = 16
   // (64-thread CTAs, eight per SM).
   static constexpr bool kQuad = (sizeof(T) == 4 && N == 32 && (C == 4 || C == 8 || C == 16) && TC == kTcNone);
+  // float64 32^3 with the spectrum in TMEM: two CTAs per SM (at most 256 registers)
   static constexpr int MIN_BLOCKS = (TC == kTcTF32 || TC == kTc3xBF16) ? 2
                                     : (TC == kTc3xTF32)                  ? 1
                                     : kQuad                              ? C / 2
+                                    : (sizeof(T) == 8 && N == 32)        ? 2
                                                                          : 1;
   using T2 = typename Vec2<T>::type;
   static constexpr bool kF32 = sizeof(T) == 4;
   // float32: the spectrum pencil of each thread is private to it (TMEM at N = 16, 32,
   // registers otherwise) and the x-plane buffer is double-buffered (one cluster barrier
   // per term) except in the 4-CTA 32^3 configuration, which trades the second buffer for
-  // occupancy; float64 (register bound) keeps the spectrum in shared memory with a single
-  // x-plane buffer.
+  // occupancy; float64 (register bound) keeps a single x-plane buffer.
   static constexpr bool kRegSpec = kF32;
   static constexpr int NXB = (kRegSpec && TC == kTcNone && !kQuad) ? 2 : 1;
-  // float32 register-FFT path: the spectrum pencil of each thread lives in TMEM (warp w:
-  // lanes 32 (w % 4) .., column group w / 4 of 2N columns) instead of 2N registers
-  // (N = 16, 32: the pencil's real and imaginary halves are whole 16-column chunks)
-  static constexpr bool kTmemSpec = kF32 && TC == kTcNone && N % 16 == 0;
-  static constexpr int TMEM_NEED = ((THREADS / 32 + 3) / 4) * 2 * N;
+  // Register-FFT paths at N = 16, 32 (float64: 32 only): the spectrum pencil of each
+  // thread lives in TMEM (warp w: lanes 32 (w % 4) .., column group w / 4) instead of
+  // registers (float32) or a shared-memory slab (float64, which then fits two CTAs per SM
+  // at 32^3; at 16^3 the slab is small and TMEM measured no faster).  A group of four
+  // warps takes GROUP_COLS columns: the N real parts, then the N imaginary parts, CPV
+  // 32-bit columns per value (a float64 value is its low and high words).
+  static constexpr bool kTmemSpec = TC == kTcNone && N % 16 == 0 && (kF32 || N == 32);
+  static constexpr int CPV = (int)(sizeof(T) / 4);
+  static constexpr int GROUP_COLS = 2 * N * CPV;
+  static constexpr int TMEM_NEED = ((THREADS / 32 + 3) / 4) * GROUP_COLS;
   static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
-  // The spectrum's columns as kTmemShare-column allocations: one when they fit in one,
-  // otherwise one per group of four warps (2N <= 64 columns each).
-  static constexpr int TMEM_SHARES = !kTmemSpec ? 0 : TMEM_NEED <= kTmemShare ? 1 : (THREADS / 32 + 3) / 4;
+  // The spectrum's columns as kTmemShare-column allocations: one when they all fit in
+  // one, otherwise SPG = GROUP_COLS / kTmemShare per group of four warps (SPG = 1: real
+  // and imaginary halves in one share; SPG = 2: one share each).
+  static constexpr int SPG = GROUP_COLS <= kTmemShare ? 1 : GROUP_COLS / kTmemShare;
+  static constexpr int TMEM_SHARES = !kTmemSpec ? 0 : TMEM_NEED <= kTmemShare ? 1 : ((THREADS / 32 + 3) / 4) * SPG;
   static_assert(!kTmemSpec || TMEM_SHARES <= 4, "spectrum shares per CTA");
-  static_assert(!kTmemSpec || TMEM_SHARES == 1 || 2 * N <= kTmemShare, "one share per warp group");
+  static_assert(!kTmemSpec || TMEM_SHARES == 1 || (SPG == 1 && GROUP_COLS <= kTmemShare) ||
+                    (SPG == 2 && GROUP_COLS == 2 * kTmemShare),
+                "whole shares per warp group");
   // x-plane buffer: the NP x-values of a slab are grouped in chunks of VEC (16 bytes:
   // two float2 or one double2); element (xl, ky, k) (k = kz or z) sits at
   // ((xl / VEC) N + ky) RW VEC + k VEC + xl % VEC.  A warp of the kx pass (lanes along
@@ -121,7 +131,7 @@ struct CollideCfg {
   static constexpr int VEC = kF32 ? 2 : 1;
   static constexpr int NCH = NP / VEC;  // chunks per (ky, k)
   static constexpr int RW = N + 1;
-  static constexpr size_t FH = kRegSpec ? 0 : (size_t)N * NP * N;  // spectrum slab [kx][kyl][kz]
+  static constexpr size_t FH = (kRegSpec || kTmemSpec) ? 0 : (size_t)N * NP * N;  // spectrum slab [kx][kyl][kz]
   static constexpr size_t XB = (size_t)NCH * N * RW * VEC;
   static constexpr size_t OFF_XB = FH * sizeof(T2);
   static constexpr size_t OFF_RED = OFF_XB + NXB * XB * sizeof(T2);
@@ -386,6 +396,45 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
       : "memory");
 }
 
+// N values of a pencil <-> consecutive TMEM columns of this thread's lane: float32 one
+// column each, float64 two (low word, then high word).  The float32 load is completed by
+// the caller's tcgen05.wait::ld; the float64 load waits after each 16 columns and then
+// assembles its 8 values, so no word is read before it has arrived.
+template <typename T, int N>
+__device__ __forceinline__ void tmem_st_pencil(uint32_t addr, const T* v) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int c = 0; c < N; c += 16) tmem_st16(addr + c, reinterpret_cast<const float*>(v) + c);
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; c += 8) {
+      float w[16];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        w[2 * k] = __int_as_float(__double2loint((double)v[c + k]));
+        w[2 * k + 1] = __int_as_float(__double2hiint((double)v[c + k]));
+      }
+      tmem_st16(addr + 2 * c, w);
+    }
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void tmem_ld_pencil(uint32_t addr, T* v) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int c = 0; c < N; c += 16) tmem_ld16(addr + c, reinterpret_cast<float*>(v) + c);
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; c += 8) {
+      float w[16];
+      tmem_ld16(addr + 2 * c, w);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[c + k] = (T)__hiloint2double(__float_as_int(w[2 * k + 1]), __float_as_int(w[2 * k]));
+    }
+  }
+}
+
 // ---- tensor-core 1D DFT of 128 pencils (tcgen05) ------------------------------------
 // Each thread of the CTA holds one pencil of N complex values.  The inverse DFT of all
 // 128 pencils is one dense contraction D[128 x 2N] = A[128 x 2N] W[2N x 2N] with the real
@@ -617,7 +666,7 @@ collide_kernel(const CollideArgs args) {
   constexpr bool kTmemSpec = Cfg::kTmemSpec;
   constexpr bool kRegArr = kRegSpec && !kTmemSpec;
   T fr[kRegArr ? N : 1], fi[kRegArr ? N : 1];  // spectrum pencil in registers (tensor-core modes)
-  uint32_t spec_addr = 0;  // spectrum pencil in TMEM (register-FFT float32)
+  uint32_t spec_re = 0, spec_im = 0;  // spectrum pencil in TMEM: real and imaginary halves
   uint32_t* spec_slots = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TSLOT);
   if constexpr (kTmemSpec) {
     // one allocation of TMEM_COLS, or one kTmemShare-column share per group of four warps
@@ -633,8 +682,17 @@ collide_kernel(const CollideArgs args) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int grp4 = threadIdx.x >> 7;  // group of four warps: lanes 0..127 of a column group
-    spec_addr = (Cfg::TMEM_SHARES == 1 ? spec_slots[0] + (uint32_t)(grp4 * 2 * N) : spec_slots[grp4]) +
-                ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
+    const uint32_t lane_off = (uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16;
+    if constexpr (Cfg::TMEM_SHARES == 1) {
+      spec_re = spec_slots[0] + (uint32_t)(grp4 * Cfg::GROUP_COLS) + lane_off;
+      spec_im = spec_re + (uint32_t)(N * Cfg::CPV);
+    } else if constexpr (Cfg::SPG == 1) {
+      spec_re = spec_slots[grp4] + lane_off;
+      spec_im = spec_re + (uint32_t)(N * Cfg::CPV);
+    } else {
+      spec_re = spec_slots[2 * grp4] + lane_off;
+      spec_im = spec_slots[2 * grp4 + 1] + lane_off;
+    }
   }
 
   // tensor-core transforms: TMEM accumulator (2N columns), completion barrier, DFT matrix
@@ -779,11 +837,8 @@ collide_kernel(const CollideArgs args) {
       }
     }
     if constexpr (kTmemSpec) {
-#pragma unroll
-      for (int c = 0; c < N; c += 16) {
-        tmem_st16(spec_addr + c, reinterpret_cast<const float*>(re) + c);
-        tmem_st16(spec_addr + N + c, reinterpret_cast<const float*>(im) + c);
-      }
+      tmem_st_pencil<T, N>(spec_re, re);
+      tmem_st_pencil<T, N>(spec_im, im);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
   }
@@ -801,11 +856,8 @@ collide_kernel(const CollideArgs args) {
   auto pass_kx = [&](int j, T2* XB) {
     const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
     if constexpr (kTmemSpec) {
-#pragma unroll
-      for (int c = 0; c < N; c += 16) {
-        tmem_ld16(spec_addr + c, reinterpret_cast<float*>(re) + c);
-        tmem_ld16(spec_addr + N + c, reinterpret_cast<float*>(im) + c);
-      }
+      tmem_ld_pencil<T, N>(spec_re, re);
+      tmem_ld_pencil<T, N>(spec_im, im);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     }
 #pragma unroll

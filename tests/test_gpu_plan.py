@@ -39,7 +39,9 @@ def _make(seed_base=300):
     grids, fs = [], []
     for i, (N, L, gamma, M, opts, prec, dt, cells) in enumerate(GROUPS):
         grids.append(B.Grid(N, L, gamma, M, **opts))
-        fs.append(torch.from_numpy(W.two_maxwellians(cells, N, L, seed_base + i)).to(device="cuda", dtype=dt))
+        f = W.two_maxwellians(cells, N, L, seed_base + i)
+        f[1::2] = W.bkw(N, L, 0.75)  # ragged batches mix BKW-type cells in
+        fs.append(torch.from_numpy(f).to(device="cuda", dtype=dt))
     return grids, fs
 
 
