@@ -95,8 +95,8 @@ typedef struct {
                         kept with the grid).  Clamped to [1, M_eff].  Results depend on G (rounding
                         order of the gain sum) but not on the batch size.               */
   int cluster_size;  /* thread-block cluster size (CTAs per cell) of the float32 path;
-                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 8, 48: 8, 64: 16).  Also
-                        built: 16: 2, 4; 24: 2, 6; 32: 4, 16.  Larger clusters give each CTA
+                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 8, 48: 12, 64: 16).  Also
+                        built: 16: 2, 4; 24: 2, 6; 32: 4, 16; 48: 8.  Larger clusters give each CTA
                         a thinner slab (fewer threads, more CTAs per SM).  The float64
                         path always uses its own size (8: 1, 16: 2, 24: 3, 32: 8).
                         Results agree across sizes up to the rounding of the moment sums

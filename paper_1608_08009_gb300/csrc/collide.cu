@@ -210,7 +210,8 @@ bool collide_supported(int N, int prec) {
 // Cluster sizes.  float64: the smallest C whose per-CTA slab fits shared memory and
 // registers.  float32: measured on GB300 -- at 32^3, C = 8 (128-thread CTAs, two clusters
 // per SM whose barrier waits overlap) beats C = 4 (one 256-thread CTA per SM) by 8 % and
-// C = 16 by 30 %; at 24^3 the autotuner prefers 3 to 2.  The other built sizes are
+// C = 16 by 30 %; at 24^3 the autotuner prefers 3 to 2; at 48^3, C = 12 (two 192-thread
+// CTAs per SM) beats C = 8 (one 288-thread CTA per SM) by 49 %.  The other built sizes are
 // candidates for the autotuner of ragged plans and for boltz_grid_opts.cluster_size.
 int default_cluster(int N, int prec) {
   const bool dbl = (prec == BOLTZ_FP64);
@@ -219,7 +220,7 @@ int default_cluster(int N, int prec) {
     case 16: return dbl ? 2 : 1;
     case 24: return 3;
     case 32: return 8;
-    case 48: return dbl ? 0 : 8;
+    case 48: return dbl ? 0 : 12;
     case 64: return dbl ? 0 : 16;
     default: return 0;
   }
@@ -241,6 +242,7 @@ int cluster_choices(int N, int prec, int* out) {
       out[k++] = 4;
       out[k++] = 16;
     }
+    if (N == 48) out[k++] = 8;
   }
   return k;
 }
@@ -368,7 +370,7 @@ boltz_status launch_collide(const boltz_grid_s* g, int64_t n_cells, int prec, in
   }
   args.tab = g->tab32;
   if (tc) return dispatch_3d_tc(g, args, n_cells, stream, prec, f_is_fp64);
-  if (g->N > 32) return dispatch_3d_large(g, args, n_cells, stream, f_is_fp64);
+  if (g->N > 32) return dispatch_3d_large(g, args, n_cells, stream, cluster, f_is_fp64);
   return dispatch_3d_f32(g, args, n_cells, stream, cluster, f_is_fp64);
 }
 

@@ -1110,11 +1110,14 @@ collide_kernel(const CollideArgs args) {
 // ------------------------------------------------------------------------------------
 // N = 48 and 64 (float32).  One pencil of 48 or 64 complex values takes 96 or 128
 // registers, so the gain accumulator and the spectrum cannot stay in registers as above:
-// each thread's spectrum pencil goes to tensor memory (TMEM, 256 KB per SM, unused by
-// this kernel otherwise; written once, read back by the same thread every term), the
-// gain accumulator of the CTA's x-slab lives in shared memory, and one x-plane buffer
-// serves every term (two cluster barriers per term).  The epilogue recomputes g in a second sweep instead of keeping N float64 values
-// per thread.  Otherwise the same decomposition and arithmetic as collide_kernel.
+// each thread's spectrum pencil goes to tensor memory (written once, read back by the
+// same thread every term, in 64-column shares), the gain accumulator of the CTA's
+// x-slab lives in shared memory, and one x-plane buffer serves every term with the
+// 32^3 kernel's exchange (st.async scatter, per-chunk waits, split write-after-read
+// barrier).  Clusters of 12 at 48^3 (4 x-planes per CTA, two CTAs per SM) and of 16 at
+// 64^3 (one CTA per SM).  The epilogue recomputes g in a second sweep instead of
+// keeping N float64 values per thread.  Otherwise the same decomposition and arithmetic
+// as collide_kernel.
 // ------------------------------------------------------------------------------------
 template <int N, int C>
 struct LargeCfg {
@@ -1129,18 +1132,23 @@ struct LargeCfg {
   static constexpr size_t OFF_ACC = XB * sizeof(float2);
   static constexpr size_t OFF_RED = OFF_ACC + ACC * sizeof(float);
   static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
-  // flag, the TMEM address, then one scatter mbarrier per chunk of the x-slab
+  // flag, then one scatter mbarrier per chunk of the x-slab, then the TMEM addresses
   static constexpr size_t OFF_MBAR = OFF_FLAG + 16;
-  static constexpr size_t SMEM = OFF_MBAR + 8 * NCH;
+  // spectrum pencils in TMEM: warp w uses lanes 32 (w % 4) .. + 31; each group of four
+  // warps holds two kTmemShare-column allocations, its N real parts in one and its N
+  // imaginary parts in the other, so the kernel follows the share rule above
+  static constexpr int GROUPS4 = (WARPS + 3) / 4;
+  static constexpr int TMEM_SHARES = 2 * GROUPS4;
+  static constexpr size_t OFF_TSLOT = OFF_MBAR + 8 * NCH;
+  static constexpr size_t SMEM = (OFF_TSLOT + 4 * TMEM_SHARES + 15) / 16 * 16;
+  // CTAs per SM: two at 48^3 with 12-CTA clusters (4 x-planes, 192 threads, 110 KB of
+  // shared memory, 4 shares), one otherwise
+  static constexpr int MIN_BLOCKS = (N == 48 && C == 12) ? 2 : 1;
   // bytes a CTA receives per term (its x-slab of one term's kx-pass outputs)
   static constexpr uint32_t SCATTER_BYTES = (uint32_t)NP * N * N * 2 * sizeof(float);
   static_assert(NCH <= 4 && (THREADS / NCH) % 32 == 0, "per-chunk mbarriers and named barriers");
-  // spectrum pencils in TMEM: warp w uses lanes 32 (w % 4) .. + 31 and the column group
-  // w / 4 of 2N columns (N real parts, then N imaginary parts)
-  static constexpr int TMEM_NEED = ((WARPS + 3) / 4) * 2 * N;
-  static constexpr int TMEM_COLS = TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
-  static_assert(TMEM_NEED <= 512, "spectrum slab fits TMEM");
-  static_assert((2 * N) % 16 == 0, "whole 16-column TMEM chunks");
+  static_assert(N <= kTmemShare && TMEM_SHARES <= 8, "real or imaginary parts of a pencil fit one share");
+  static_assert(N % 16 == 0, "whole 16-column TMEM chunks");
   static_assert(THREADS % 32 == 0 && NP % VEC == 0, "whole warps and chunks");
   static_assert(OFF_RED % 16 == 0, "aligned reduction area");
   static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -1150,7 +1158,8 @@ struct LargeCfg {
 };
 
 template <typename TIO, int N, int C, bool kSplit>
-__global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kernel(const CollideArgs args) {
+__global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, LargeCfg<N, C>::MIN_BLOCKS)
+    collide_large_kernel(const CollideArgs args) {
   using Cfg = LargeCfg<N, C>;
   using T = float;
   using T2 = float2;
@@ -1189,17 +1198,20 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   const TIO* fin = cell_input<TIO>(args, cell, x_own, n);
   // this thread's spectrum pencil (its (ky, kz), all kx) in TMEM, written once by the
   // forward x pass and read back in every kx pass
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_FLAG + 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + Cfg::OFF_TSLOT);
   if ((t >> 5) == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(Cfg::TMEM_COLS));
+#pragma unroll
+    for (int k = 0; k < Cfg::TMEM_SHARES; ++k)
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot + k)),
+                   "r"(kTmemShare));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem_base = *tmem_slot;
-  const uint32_t spec_addr = tmem_base + ((uint32_t)(32 * ((t >> 5) & 3)) << 16) + (uint32_t)((t >> 7) * 2 * N);
+  const uint32_t lane_off = (uint32_t)(32 * ((t >> 5) & 3)) << 16;
+  const uint32_t spec_re = tmem_slot[2 * (t >> 7)] + lane_off, spec_im = tmem_slot[2 * (t >> 7) + 1] + lane_off;
   // Exchange per term as in collide_kernel's 32^3 single-buffer form: st.async scatter
   // completing on one mbarrier per chunk of the owner's x-slab (chunk c: planes c VEC ..,
   // whose kz and ky passes are done by threads [c THREADS / NCH, ...) alone), armed for
@@ -1289,8 +1301,8 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
     }
 #pragma unroll
     for (int c = 0; c < N; c += 16) {
-      tmem_st16(spec_addr + c, re + c);
-      tmem_st16(spec_addr + N + c, im + c);
+      tmem_st16(spec_re + c, re + c);
+      tmem_st16(spec_im + c, im + c);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
@@ -1312,8 +1324,8 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
       const T2* tj = tab + (size_t)j * n + (size_t)ky_own * N * N + kzt;
 #pragma unroll
       for (int c = 0; c < N; c += 16) {
-        tmem_ld16(spec_addr + c, re + c);
-        tmem_ld16(spec_addr + N + c, im + c);
+        tmem_ld16(spec_re + c, re + c);
+        tmem_ld16(spec_im + c, im + c);
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
@@ -1387,8 +1399,11 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, 1) collide_large_kern
   // the spectrum is no longer needed: free the TMEM columns
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if ((t >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(Cfg::TMEM_COLS));
+  if ((t >> 5) == 0) {
+#pragma unroll
+    for (int k = 0; k < Cfg::TMEM_SHARES; ++k)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot[k]), "r"(kTmemShare));
+  }
 
   const int x = x_own, z = zt;
   float* acc_row = accs + (size_t)xlt * N * N + z;  // acc_row[y * N], this thread's (x, z) row
@@ -1856,7 +1871,7 @@ static boltz_status launch_large_impl(const CollideArgs& a, int64_t n_cells, cud
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const unsigned long long bit = 1ull << (dev & 63);
   size_t smem = Cfg::SMEM;
-  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_COLS, Cfg::SMEM, dev, &smem);
+  const boltz_status ss = tmem_launch_smem(Cfg::TMEM_SHARES * kTmemShare, Cfg::SMEM, dev, &smem, Cfg::TMEM_SHARES);
   if (ss != BOLTZ_OK) return ss;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -27,13 +27,17 @@ boltz_status dispatch_3d_tc(const boltz_grid_s* g, const CollideArgs& a, int64_t
 
 // N = 48, 64 (float32 only)
 boltz_status dispatch_3d_large(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
-                               int f_is_fp64) {
-  if (g->N == 48)
+                               int cluster, int f_is_fp64) {
+  const int C = cluster > 0 ? cluster : default_cluster(g->N, BOLTZ_FP32_FFT);
+  if (g->N == 48 && C == 8)
     return f_is_fp64 ? launch_large_impl<double, 48, 8>(a, n_cells, st) : launch_large_impl<float, 48, 8>(a, n_cells, st);
-  if (g->N == 64)
+  if (g->N == 48 && C == 12)
+    return f_is_fp64 ? launch_large_impl<double, 48, 12>(a, n_cells, st)
+                     : launch_large_impl<float, 48, 12>(a, n_cells, st);
+  if (g->N == 64 && C == 16)
     return f_is_fp64 ? launch_large_impl<double, 64, 16>(a, n_cells, st)
                      : launch_large_impl<float, 64, 16>(a, n_cells, st);
-  set_error("no large-N kernel for this N");
+  set_error("no large-N kernel for this (N, cluster size)");
   return BOLTZ_EUNSUPPORTED;
 }
 

@@ -175,7 +175,7 @@ boltz_status dispatch_3d_f64(const boltz_grid_s* g, const CollideArgs& a, int64_
 boltz_status dispatch_3d_tc(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st, int prec,
                             int f_is_fp64);
 boltz_status dispatch_3d_large(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
-                               int f_is_fp64);
+                               int cluster, int f_is_fp64);
 boltz_status dispatch_2d(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st, int prec,
                          int f_is_fp64);
 #define BOLTZ_DECLARE_UNIT(TAG)                                                                                    \

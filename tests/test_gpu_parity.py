@@ -310,7 +310,8 @@ def test_full_size_mixed_sampled():
 
 
 @pytest.mark.parametrize("N,L,C", [(16, 6.0, 1), (16, 6.0, 2), (16, 6.0, 4), (24, 7.0, 2), (24, 7.0, 3),
-                                   (24, 7.0, 6), (32, 8.0, 4), (32, 8.0, 8), (32, 8.0, 16)])
+                                   (24, 7.0, 6), (32, 8.0, 4), (32, 8.0, 8), (32, 8.0, 16), (48, 8.0, 8),
+                                   (48, 8.0, 12)])
 def test_every_cluster_size_parity(N, L, C):
     """Every cluster size the float32 path dispatches (boltz_grid_opts.cluster_size), each
     against the oracle: collide with float64 and float32 storage, and Euler / Heun relax
