@@ -1680,22 +1680,27 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
   const int x = t;
   const double vx = -L + x * dv;
   const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
-  auto gval = [&](int y) {
-    const TIO fv = fin[x * N + y];
-    const T q = acc[y] - (T)fv * re[y];
-    double gv = args.s * (double)q;
-    if (args.b != 0.0) gv += args.b * (double)fv;
-    if (fb) gv += args.a * (double)fb[x * N + y];
-    return gv;
-  };
-  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+  // g = s Q + b f (+ a f_base) along this row; Q = Q+ - f L rounded once in T
+  auto qval = [&](int y) { return (double)(acc[y] - (T)fin[x * N + y] * re[y]); };
+  // Phi g over the row: the f part is b times the forward pass's sums s0, s1, s2 of the
+  // same row, so only Q (and f_base) is summed here (the FP64 pipe bounds this kernel)
+  double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, F0 = 0.0, F1 = 0.0, F2 = 0.0;
 #pragma unroll
   for (int y = 0; y < N; ++y) {
-    const double gv = gval(y);
-    S0 += gv;
-    S1 += (double)y * gv;
-    S2 += (double)(y * y) * gv;
+    const double qv = qval(y);
+    Q0 += qv;
+    Q1 += (double)y * qv;
+    Q2 += (double)(y * y) * qv;
+    if (fb) {
+      const double bv = (double)fb[x * N + y];
+      F0 += bv;
+      F1 += (double)y * bv;
+      F2 += (double)(y * y) * bv;
+    }
   }
+  const double S0 = args.s * Q0 + args.b * s0 + args.a * F0;
+  const double S1 = args.s * Q1 + args.b * s1 + args.a * F1;
+  const double S2 = args.s * Q2 + args.b * s2 + args.a * F2;
   // this row's share of Phi g and Phi f (targets), v_y = -L + y dv; slot 3 (v_z) is zero
   {
     double* r = red + t * 10;
@@ -1742,14 +1747,21 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
   }
   TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
   bool bad = false;
+  // Phi^T c at (vx, vy) = P0 + R(y), R(y) = y (P1 + y P2) the same for every row of the
+  // cell: thread t writes R(t) over its row sums (read above), the row adds its own P0
   const double P0 = c5[0] + c5[1] * vx + 0.5 * c5[4] * (vx * vx + L * L) - c5[2] * L;
   const double P1 = (c5[2] - c5[4] * L) * dv;
   const double P2 = 0.5 * c5[4] * dv * dv;
+  red[t] = (double)t * (P1 + (double)t * P2);
+  cell_sync();
 #pragma unroll
   for (int y = 0; y < N; ++y) {
-    const double val = gval(y) + (P0 + (double)y * (P1 + (double)y * P2));
+    const int idx = x * N + y;
+    double val = fma(args.b, (double)fin[idx], P0 + red[y]);
+    if (fb) val = fma(args.a, (double)fb[idx], val);
+    val = fma(args.s, qval(y), val);
     bad |= !isfinite(val);
-    if (writable) out[x * N + y] = (TIO)val;
+    if (writable) out[idx] = (TIO)val;
   }
   if (bad && writable) atomicOr(&g_boltz_status, kStatusNonFinite);
 }
