@@ -387,6 +387,16 @@ boltz_status boltz_stream_status(void* stream);
 /* Thread-local message of the last failing call of this thread ("" if none). */
 const char* boltz_last_error(void);
 
+/* Self-check of the library's own float <-> double conversions, which the 2D kernel
+ * runs on the integer pipes because GB300 issues the hardware conversions to its narrow
+ * FP64 pipe.  Compares them with the hardware conversions on the current device:
+ * float -> double on all 2^32 float bit patterns, double -> float (round to nearest
+ * even) on 2^32 pseudo-random doubles and on the ties and near-ties between neighbouring
+ * floats.  mismatches: host array of 2 counts (float -> double, double -> float); both
+ * 0 when the conversions are exact.  Synchronous; allocates 16 bytes of device memory.
+ * Errors: EINVAL (null pointer), ENOMEM, ECUDA. */
+boltz_status boltz_selftest_conversions(uint64_t* mismatches);
+
 /* Grid description for callers and tests.  Any output pointer may be NULL.
  *   S, R       support radius and Carleman radius; M_eff = M_dirs * radial_rank. */
 boltz_status boltz_grid_info(boltz_grid g, int* N_v, double* L, double* dv, double* S,

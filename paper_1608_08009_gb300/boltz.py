@@ -40,7 +40,7 @@ EXPORTED = ("boltz_default_opts", "boltz_create_grid", "boltz_destroy_grid", "bo
             "boltz_server_pump", "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_host_chunks",
             "boltz_server_submit_batch", "boltz_server_stats_get", "boltz_fks_create", "boltz_fks_step",
             "boltz_fks_time", "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy",
-            "boltz_plan_group_precision")
+            "boltz_plan_group_precision", "boltz_selftest_conversions")
 
 
 class BoltzError(RuntimeError):
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         L.boltz_fks_shifts.argtypes = [vp, f64, P(i32)]
         L.boltz_fks_destroy.argtypes = [vp]
         L.boltz_plan_group_precision.argtypes = [vp, i32, P(i32)]
+        L.boltz_selftest_conversions.argtypes = [P(ctypes.c_uint64)]
         L.boltz_server_step.argtypes = [vp, P(i32), P(i32)]
         L.boltz_server_pump.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.boltz_server_checkpoint.argtypes = [vp, i64, vp, P(i32)]
@@ -136,7 +137,8 @@ def lib() -> ctypes.CDLL:
                      "boltz_plan_group_info", "boltz_plan_destroy", "boltz_server_pump",
                      "boltz_create_grid2d", "boltz_server_checkpoint", "boltz_server_submit_batch",
                      "boltz_server_stats_get", "boltz_fks_create", "boltz_fks_step", "boltz_fks_time",
-                     "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy", "boltz_plan_group_precision"):
+                     "boltz_fks_set_time", "boltz_fks_shifts", "boltz_fks_destroy", "boltz_plan_group_precision",
+                     "boltz_selftest_conversions"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -237,6 +239,14 @@ def boltz_stream_status(stream=None) -> None:
 
 def boltz_last_error() -> str:
     return lib().boltz_last_error().decode()
+
+
+def boltz_selftest_conversions() -> tuple:
+    """(float->double mismatches, double->float mismatches) of the library's integer-pipe
+    conversions against the hardware ones on the current device."""
+    out = (ctypes.c_uint64 * 2)()
+    _check(lib().boltz_selftest_conversions(out))
+    return int(out[0]), int(out[1])
 
 
 def boltz_version() -> str:

@@ -347,6 +347,14 @@ boltz_status boltz_moments(const boltz_batch* b, const void* f, double* U, void*
   return boltz::launch_phisums(b->grid, b->n_cells, b->f_is_fp64, f, U, vol, (cudaStream_t)stream);
 }
 
+boltz_status boltz_selftest_conversions(uint64_t* mismatches) {
+  if (!mismatches) {
+    set_error("null mismatches");
+    return BOLTZ_EINVAL;
+  }
+  return boltz::selftest_conversions(mismatches);
+}
+
 boltz_status boltz_relax(const boltz_batch* b, void* f, double dt, int steps, int rk_order, void* stream) {
   boltz_status st = check_batch(b);
   if (st != BOLTZ_OK) return st;

@@ -219,6 +219,58 @@ __device__ __forceinline__ P* cta_smem(P* p, int r) {
   }
 }
 
+// float -> double by moving the IEEE 754 fields on the integer pipes (binary32 to
+// binary64: exponent rebiased by 1023 - 127 = 896, fraction shifted left by 29;
+// subnormals normalised with a leading-zero count; zeros, infinities and NaNs keep their
+// class).  Exact, like the hardware conversion, which on GB300 issues to the FP64 pipe
+// (1/64 of the FP32 rate).  Used where that pipe binds (the 2D kernel); in the 3D
+// kernels, bound by latency and issue instead, the extra integer instructions measured
+// slower and the hardware conversion stays.
+template <typename X>
+__device__ __forceinline__ double to_f64(X x) {
+  return (double)x;
+}
+template <>
+__device__ __forceinline__ double to_f64<float>(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xffu, s = u & 0x80000000u;
+  uint32_t hi = s | (((u & 0x7fffffffu) >> 3) + 0x38000000u), lo = u << 29;
+  if (e == 0xffu) hi |= 0x7ff00000u;  // infinity / NaN: all-ones exponent
+  if (e == 0u) {
+    const uint32_t m = u & 0x7fffffu;
+    if (m == 0u) {
+      hi = s;
+      lo = 0u;
+    } else {  // subnormal m 2^-149: normalise to 1.f 2^(-126 - sh)
+      const int sh = __clz((int)m) - 8;
+      const uint32_t mn = m << sh;
+      hi = s | ((uint32_t)(897 - sh) << 20) | ((mn & 0x7fffffu) >> 3);
+      lo = mn << 29;
+    }
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float, rounded to nearest (ties to even), on the integer pipes for results in
+// the normal float range: the 23 fraction bits are the top of the double's 52, the 29
+// dropped bits decide the rounding, and a carry out of the fraction steps the exponent
+// (up to infinity, as the rounding requires).  Zeros, float subnormals, overflow,
+// infinities and NaNs take the hardware conversion.
+template <typename X>
+__device__ __forceinline__ X from_f64(double d) {
+  return (X)d;
+}
+template <>
+__device__ __forceinline__ float from_f64<float>(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // float biased exponent
+  if (e < 1 || e > 254) return (float)d;
+  uint32_t r = (hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1fffffffu, half = 0x10000000u;
+  r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1585,9 +1637,10 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
     const TIO fv = fin[t * N + y];
     re[y] = (T)fv;
     im[y] = T(0);
-    s0 += (double)fv;
-    s1 += (double)y * (double)fv;
-    s2 += (double)(y * y) * (double)fv;
+    const double fd = to_f64(fv);
+    s0 += fd;
+    s1 += (double)y * fd;
+    s2 += (double)(y * y) * fd;
   }
   fft_regs<N, -1>(re, im);
 #pragma unroll
@@ -1681,7 +1734,7 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
   const double vx = -L + x * dv;
   const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
   // g = s Q + b f (+ a f_base) along this row; Q = Q+ - f L rounded once in T
-  auto qval = [&](int y) { return (double)(acc[y] - (T)fin[x * N + y] * re[y]); };
+  auto qval = [&](int y) { return to_f64(acc[y] - (T)fin[x * N + y] * re[y]); };
   // Phi g over the row: the f part is b times the forward pass's sums s0, s1, s2 of the
   // same row, so only Q (and f_base) is summed here (the FP64 pipe bounds this kernel)
   double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, F0 = 0.0, F1 = 0.0, F2 = 0.0;
@@ -1692,7 +1745,7 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
     Q1 += (double)y * qv;
     Q2 += (double)(y * y) * qv;
     if (fb) {
-      const double bv = (double)fb[x * N + y];
+      const double bv = to_f64(fb[x * N + y]);
       F0 += bv;
       F1 += (double)y * bv;
       F2 += (double)(y * y) * bv;
@@ -1757,11 +1810,11 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
 #pragma unroll
   for (int y = 0; y < N; ++y) {
     const int idx = x * N + y;
-    double val = fma(args.b, (double)fin[idx], P0 + red[y]);
-    if (fb) val = fma(args.a, (double)fb[idx], val);
+    double val = fma(args.b, to_f64(fin[idx]), P0 + red[y]);
+    if (fb) val = fma(args.a, to_f64(fb[idx]), val);
     val = fma(args.s, qval(y), val);
     bad |= !isfinite(val);
-    if (writable) out[idx] = (TIO)val;
+    if (writable) out[idx] = from_f64<TIO>(val);
   }
   if (bad && writable) atomicOr(&g_boltz_status, kStatusNonFinite);
 }

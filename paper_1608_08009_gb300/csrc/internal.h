@@ -178,6 +178,7 @@ boltz_status dispatch_3d_large(const boltz_grid_s* g, const CollideArgs& a, int6
                                int cluster, int f_is_fp64);
 boltz_status dispatch_2d(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st, int prec,
                          int f_is_fp64);
+boltz_status selftest_conversions(uint64_t* mismatches);
 #define BOLTZ_DECLARE_UNIT(TAG)                                                                                    \
   cudaError_t unit_upload_twiddles_##TAG(const TwiddleTables& t);                                                 \
   cudaError_t unit_read_clear_status_##TAG(unsigned* value);
