@@ -405,11 +405,6 @@ def run_serving(seconds: float, rate: float = 200.0, seed: int = 20165, budget_b
 RAGGED_L = {16: 6.0, 24: 7.0, 32: 8.0, 48: 8.0}
 
 
-def ragged_groups(wl: dict):
-    """Seeded per-cell (N, M, gamma) of the ragged batch, grouped: {(N, M, gamma): cells}."""
-    return {k: len(v) for k, v in ragged_cells(wl).items()}
-
-
 def ragged_cells(wl: dict):
     """Seeded per-cell draws of the ragged batch, grouped by (N, M, gamma): for each cell
     of a group its initial datum, None for a two-Maxwellian cell, else the BKW shape
