@@ -84,6 +84,27 @@ def test_direction_weights(kind):
         assert abs(np.sum(w * e[:, 0] ** 2 * e[:, 1] ** 2) - 2 * math.pi / 15) < 1e-13
 
 
+@pytest.mark.parametrize("A", [8, 16, 32])
+def test_product_grid_is_the_midpoint_rule_in_theta(A):
+    """kind 0 (the paper's product grid, midpoint reading, weight sin(theta)): with
+    Delta = pi / A the composite midpoint rule in theta has the Euler-Maclaurin error
+    -(Delta^2 / 24) (h'(pi) - h'(0)) + O(Delta^4) and the midpoints in varphi integrate
+    cos^2, sin^2 exactly, so on the half sphere
+      sum w        = 2 pi (1 + Delta^2 / 24) + O(Delta^4)     (h = sin)
+      sum w e_x^2  = 2 pi / 3 + O(Delta^4)                   (h = sin^3, h'(0) = h'(pi) = 0)
+      sum w e_z^2  = (2 pi / 3)(1 + Delta^2 / 8) + O(Delta^4)  (h = cos^2 sin).
+    An endpoint placement of theta (p pi / A) flips the sign of the Delta^2 terms, a
+    dropped sin(theta) weight changes the leading terms."""
+    e, w = G.directions(A * A, 0)
+    d = math.pi / A
+    assert abs(w.sum() - 2 * math.pi * (1 + d * d / 24)) < 0.1 * d ** 4
+    assert abs(np.sum(w * e[:, 0] ** 2) - 2 * math.pi / 3) < 0.1 * d ** 4
+    assert abs(np.sum(w * e[:, 1] ** 2) - 2 * math.pi / 3) < 0.1 * d ** 4
+    assert abs(np.sum(w * e[:, 2] ** 2) - 2 * math.pi / 3 * (1 + d * d / 8)) < 0.1 * d ** 4
+    # varphi in [0, pi) halves the sphere across y: e_y > 0, both signs of e_x and e_z
+    assert np.all(e[:, 1] > 0) and np.any(e[:, 0] < 0) and np.any(e[:, 2] < 0)
+
+
 def test_kernel_l0_closed_form():
     """K(0, m) -> B_F(0, m) = Btilde 4 pi^2 R^2 (1 - cos R|xi|)/|xi|^2 (Eq. FKM)."""
     g = O.make_grid(16, 6.0, M=256, dirs_kind=2)
