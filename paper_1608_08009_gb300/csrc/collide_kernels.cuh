@@ -448,9 +448,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
       : "memory");
 }
 
+// tcgen05.wait::ld with the 16 destination registers of an earlier tcgen05.ld as in-out
+// operands.  The registers of a TMEM load hold their values only once the wait has
+// completed, and a plain wait orders memory operations alone: arithmetic that reads the
+// registers could be scheduled above it.  Tied to the wait, every reader depends on it.
+// The first wait blocks until all of the thread's loads have completed; the ones after it
+// only tie their registers.
+__device__ __forceinline__ void tmem_wait_ld16(float* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+// The wait for K (a multiple of 16) float32 registers filled by tmem_ld16.
+template <int K>
+__device__ __forceinline__ void tmem_wait_ld(float* v) {
+  static_assert(K % 16 == 0, "whole 16-column loads");
+#pragma unroll
+  for (int c = 0; c < K; c += 16) tmem_wait_ld16(v + c);
+}
+
 // N values of a pencil <-> consecutive TMEM columns of this thread's lane: float32 one
 // column each, float64 two (low word, then high word).  The float32 load is completed by
-// the caller's tcgen05.wait::ld; the float64 load waits after each 16 columns and then
+// the caller's tmem_wait_pencil; the float64 load waits after each 16 columns and then
 // assembles its 8 values, so no word is read before it has arrived.
 template <typename T, int N>
 __device__ __forceinline__ void tmem_st_pencil(uint32_t addr, const T* v) {
@@ -480,10 +508,19 @@ __device__ __forceinline__ void tmem_ld_pencil(uint32_t addr, T* v) {
     for (int c = 0; c < N; c += 8) {
       float w[16];
       tmem_ld16(addr + 2 * c, w);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tmem_wait_ld16(w);
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[c + k] = (T)__hiloint2double(__float_as_int(w[2 * k + 1]), __float_as_int(w[2 * k]));
     }
+  }
+}
+// Completes tmem_ld_pencil of a real and an imaginary pencil (float32: the tied wait;
+// float64 pencils have been assembled after their own waits).
+template <typename T, int N>
+__device__ __forceinline__ void tmem_wait_pencil(T* re, T* im) {
+  if constexpr (sizeof(T) == 4) {
+    tmem_wait_ld<N>(reinterpret_cast<float*>(re));
+    tmem_wait_ld<N>(reinterpret_cast<float*>(im));
   }
 }
 
@@ -656,7 +693,7 @@ struct TcDft {
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
             "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(lane_base + c));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tmem_wait_ld16(r);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int col = c + j;
@@ -910,7 +947,7 @@ collide_kernel(const CollideArgs args) {
     if constexpr (kTmemSpec) {
       tmem_ld_pencil<T, N>(spec_re, re);
       tmem_ld_pencil<T, N>(spec_im, im);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tmem_wait_pencil<T, N>(re, im);
     }
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
@@ -1379,7 +1416,8 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, LargeCfg<N, C>::MIN_B
         tmem_ld16(spec_re + c, re + c);
         tmem_ld16(spec_im + c, im + c);
       }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tmem_wait_ld<N>(re);
+      tmem_wait_ld<N>(im);
 #pragma unroll
       for (int kx = 0; kx < N; ++kx) {
         const float cr = re[kx], cim = im[kx];
@@ -1687,7 +1725,8 @@ collide2d_kernel(const CollideArgs args, long long n_cells) {
         tmem_ld16(spec_addr + c, reinterpret_cast<float*>(re) + c);
         tmem_ld16(spec_addr + N + c, reinterpret_cast<float*>(im) + c);
       }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tmem_wait_ld<N>(reinterpret_cast<float*>(re));
+      tmem_wait_ld<N>(reinterpret_cast<float*>(im));
     }
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) {
