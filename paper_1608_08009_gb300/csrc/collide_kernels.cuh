@@ -468,12 +468,27 @@ __device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
                :
                : "memory");
 }
-// The wait for K (a multiple of 16) float32 registers filled by tmem_ld16.
+__device__ __forceinline__ void tmem_wait_ld32(float* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]),
+                 "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]),
+                 "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
+               :
+               : "memory");
+}
+// The wait for K (a multiple of 16) float32 registers filled by tmem_ld16, tied 32 at a
+// time where K allows (with 16-register waits only, the 32^2 plane kernel spilled 8 bytes).
 template <int K>
 __device__ __forceinline__ void tmem_wait_ld(float* v) {
   static_assert(K % 16 == 0, "whole 16-column loads");
+  if constexpr (K % 32 == 0) {
 #pragma unroll
-  for (int c = 0; c < K; c += 16) tmem_wait_ld16(v + c);
+    for (int c = 0; c < K; c += 32) tmem_wait_ld32(v + c);
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; c += 16) tmem_wait_ld16(v + c);
+  }
 }
 
 // N values of a pencil <-> consecutive TMEM columns of this thread's lane: float32 one
