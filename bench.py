@@ -103,7 +103,7 @@ TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-cor
 # cells (float32 path) and 512 cells (float64 path) of the same workload, divided by the
 # cells of that capture (traffic grows in proportion to the cells: one read of f and one
 # write of the result per cell).  None when the kernel has changed since the capture.
-NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (286.781952e6 + 215.676672e6) / 2048, "fp64": (177.630976e6 + 97.723136e6) / 512}
+NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (287.785216e6 + 216.258304e6) / 2048, "fp64": (177.630976e6 + 97.723136e6) / 512}
 
 
 def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
