@@ -515,7 +515,7 @@ def test_term_groups_independent_of_batch_size_and_indexed():
 @pytest.mark.parametrize("N,L,M,groups", [(48, 8.0, 8, 1), (64, 8.0, 8, 1), (48, 8.0, 8, 3), (64, 8.0, 4, 4),
                                           (48, 8.0, 64, 1), (64, 8.0, 64, 1)])
 def test_large_grids_parity(N, L, M, groups):
-    """48^3 and 64^3 (float32 only: spectrum pencils in global scratch, gain accumulator in
+    """48^3 and 64^3 (float32 only: spectrum pencils in tensor memory, gain accumulator in
     shared memory): collide within the float32 bound, one Euler step of relax, and the
     split launch; float64 is reported unsupported."""
     cells = 2
