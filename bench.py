@@ -102,8 +102,10 @@ TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-cor
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as built, on 2048
 # cells (float32 path) and 512 cells (float64 path) of the same workload, divided by the
 # cells of that capture (traffic grows in proportion to the cells: one read of f and one
-# write of the result per cell).  None when the kernel has changed since the capture.
-NCU_DRAM_BYTES_PER_CELL = {"fp32_fft": (287.785216e6 + 216.258304e6) / 2048, "fp64": (177.630976e6 + 97.723136e6) / 512}
+# write of the result per cell), keyed by (precision, f stored float64).  None when the
+# kernel or the storage type differs from the capture.
+NCU_DRAM_BYTES_PER_CELL = {("fp32_fft", False): (287.785216e6 + 216.258304e6) / 2048,
+                           ("fp64", True): (177.630976e6 + 97.723136e6) / 512}
 
 
 def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
@@ -974,7 +976,7 @@ def run_ours(args, wl):
             "config": config_of(args, wl),
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": ((NCU_DRAM_BYTES_PER_CELL.get(wl["prec"]) or 0) * cells or None) if dim == 3
+                         "traffic": ((NCU_DRAM_BYTES_PER_CELL.get((wl["prec"], bool(wl["f64"]))) or 0) * cells or None) if dim == 3
                          and N == 32 else None,
                          "traffic_unit": "bytes per launch (ncu dram read+write, scaled by cells)",
                          "algorithmic_bytes": 2 * N ** dim * (8 if wl["f64"] else 4) * cells,

@@ -1232,7 +1232,11 @@ struct LargeCfg {
   static constexpr int NCH = NP / VEC;
   static constexpr int RW = N + 1;
   static constexpr size_t XB = (size_t)NCH * N * RW * VEC;        // float2
-  static constexpr size_t ACC = (size_t)NP * N * N;               // float, [xl][y][z]
+  // gain accumulator [xl][y][z], float; consecutive x-planes ACC_PLANE floats apart, with
+  // ACC_PLANE = 16 (mod 32) so that the two x-values of a warp (lanes ordered (x % 2, z))
+  // fall in opposite halves of the 32 banks (an N^2 stride, 0 mod 32, put them in one)
+  static constexpr int ACC_PLANE = N * N + ((16 - (N * N) % 32) + 32) % 32;
+  static constexpr size_t ACC = (size_t)NP * ACC_PLANE;
   static constexpr size_t OFF_ACC = XB * sizeof(float2);
   static constexpr size_t OFF_RED = OFF_ACC + ACC * sizeof(float);
   static constexpr size_t OFF_FLAG = OFF_RED + (size_t)(WARPS + 2) * 5 * sizeof(double);
@@ -1255,6 +1259,7 @@ struct LargeCfg {
   static_assert(N % 16 == 0, "whole 16-column TMEM chunks");
   static_assert(THREADS % 32 == 0 && NP % VEC == 0, "whole warps and chunks");
   static_assert(OFF_RED % 16 == 0, "aligned reduction area");
+  static_assert(ACC_PLANE % 32 == 16 && ACC_PLANE >= N * N, "x-planes of the accumulator in opposite bank halves");
   static_assert(SMEM <= 232448, "shared memory per CTA");
   static __device__ __forceinline__ int elem(int xl, int ky, int k) {
     return ((xl / VEC) * N + ky) * RW * VEC + k * VEC + xl % VEC;
@@ -1411,7 +1416,7 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, LargeCfg<N, C>::MIN_B
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   {  // this thread's row of the gain accumulator
-    float* a = accs + (size_t)xlt * N * N + zt;
+    float* a = accs + (size_t)xlt * Cfg::ACC_PLANE + zt;
 #pragma unroll
     for (int y = 0; y < N; ++y) a[y * N] = 0.f;
   }
@@ -1482,7 +1487,7 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, LargeCfg<N, C>::MIN_B
       }
       fft_regs<N, +1>(re, im);
       if (j < M_eff) {
-        float* a = accs + (size_t)xlt * N * N + zt;
+        float* a = accs + (size_t)xlt * Cfg::ACC_PLANE + zt;
 #pragma unroll
         for (int y = 0; y < N; ++y) a[y * N] += wj * (re[y] * im[y]);
       }
@@ -1511,7 +1516,7 @@ __global__ void __launch_bounds__(LargeCfg<N, C>::THREADS, LargeCfg<N, C>::MIN_B
   }
 
   const int x = x_own, z = zt;
-  float* acc_row = accs + (size_t)xlt * N * N + z;  // acc_row[y * N], this thread's (x, z) row
+  float* acc_row = accs + (size_t)xlt * Cfg::ACC_PLANE + z;  // acc_row[y * N], this thread's (x, z) row
   if constexpr (kSplit) {
     // partial gain and loss of this group, then the last-arrival count (as collide_kernel)
     T* part;
