@@ -105,7 +105,7 @@ TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-cor
 # write of the result per cell), keyed by (precision, f stored float64).  None when the
 # kernel or the storage type differs from the capture.
 NCU_DRAM_BYTES_PER_CELL = {("fp32_fft", False): (287.785216e6 + 216.258304e6) / 2048,
-                           ("fp64", True): (177.630976e6 + 97.723136e6) / 512}
+                           ("fp64", True): (176.368896e6 + 97.058304e6) / 512}
 
 
 def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
