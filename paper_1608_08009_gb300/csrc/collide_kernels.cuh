@@ -1623,7 +1623,6 @@ struct PlaneCfg {
   static_assert(OFF_TSLOT % 8 == 0, "aligned TMEM address slots");
   static_assert(CPB >= 1, "one cell must fit");
   static_assert(N <= 32 || CPB <= 15, "one named barrier per cell (ids 1..15)");
-  static_assert((2 * BUF * sizeof(T2)) % 16 == 0 || true, "");
 };
 
 template <typename T, typename TIO, int N>
