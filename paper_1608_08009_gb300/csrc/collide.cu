@@ -241,6 +241,7 @@ int cluster_choices(int N, int prec, int* out) {
     if (N == 32) {
       out[k++] = 4;
       out[k++] = 16;
+      out[k++] = 1;  // one CTA per cell (no term groups)
     }
     if (N == 48) out[k++] = 8;
   }

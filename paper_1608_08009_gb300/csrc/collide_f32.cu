@@ -1,6 +1,7 @@
 // Kernel unit: float32 register-FFT collision kernels for N = 8, 16, 24, 32 (all cluster sizes,
-// with and without term groups).
+// with and without term groups; at 32^3 also one CTA per cell, collide_solo.cuh).
 #include "collide_kernels.cuh"
+#include "collide_solo.cuh"
 
 namespace boltz {
 
@@ -23,6 +24,7 @@ static boltz_status dispatch_n_impl(const boltz_grid_s* g, const CollideArgs& a,
     if (g->N == 24 && C == 2) return launch_impl<T, TIO, 24, 2>(a, n_cells, st);
     if (g->N == 24 && C == 3) return launch_impl<T, TIO, 24, 3>(a, n_cells, st);
     if (g->N == 24 && C == 6) return launch_impl<T, TIO, 24, 6>(a, n_cells, st);
+    if (g->N == 32 && C == 1) return launch_solo_impl<TIO>(a, n_cells, st);
     if (g->N == 32 && C == 4) return launch_impl<T, TIO, 32, 4>(a, n_cells, st);
     if (g->N == 32 && C == 8) return launch_impl<T, TIO, 32, 8>(a, n_cells, st);
     if (g->N == 32 && C == 16) return launch_impl<T, TIO, 32, 16>(a, n_cells, st);

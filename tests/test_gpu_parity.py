@@ -342,6 +342,51 @@ def test_every_cluster_size_parity(N, L, C):
                 assert rel_l2(ft.cpu().numpy() - f, ref - f) <= tol_relax, (groups, rk)
 
 
+def test_one_cta_per_cell_32_parity():
+    """The 32^3 float32 kernel without a cluster (cluster_size 1: one CTA per cell, the
+    spectrum half and the gain accumulator in TMEM, each inverse transform in two halves
+    of x): collide with float64 and float32 storage and Euler / Heun relax against the
+    oracle (bounds as in test_every_cluster_size_parity), the headline M = 64 directions,
+    outputs poisoned with NaN all written, reruns bitwise identical, indexed cells equal
+    to the contiguous batch, term groups reported unsupported."""
+    N, L = 32, 8.0
+    for M, cells, seed in ((24, 3, 171), (64, 2, 172)):
+        dt = 0.004
+        f = W.two_maxwellians(cells, N, L, seed=seed)
+        og = oracle_grid(N, L, M)
+        Qref = O.collide(f, og)
+        tol = fp32_tol(f, og)
+        tol_relax = tol * (1.0 + dt * float(np.abs(O.operator.gain_loss(f, og)[1]).max()))
+        f32 = f.astype(np.float32).astype(np.float64)
+        Qref32 = O.collide(f32, og)
+        with B.Grid(N, L, 1.0, M, cluster_size=1) as g:
+            assert rel_l2(run_collide(g, f, B.BOLTZ_FP32_FFT), Qref) <= tol
+            assert rel_l2(run_collide(g, f.astype(np.float32), B.BOLTZ_FP32_FFT, fp64=False), Qref32) <= tol + EPS32
+            for rk in (1, 2):
+                ref = O.relax(f, og, dt, 2, rk_order=rk)
+                ft = torch.from_numpy(f).cuda()
+                B.boltz_relax(g.batch(cells, B.BOLTZ_FP32_FFT), ft, dt, 2, rk)
+                B.boltz_stream_status()
+                assert rel_l2(ft.cpu().numpy() - f, ref - f) <= tol_relax, rk
+            fd = torch.from_numpy(f.astype(np.float32)).cuda()
+            Q1 = torch.full_like(fd, float("nan"))
+            Q2 = torch.full_like(fd, float("nan"))
+            B.boltz_collide(g.batch(cells, B.BOLTZ_FP32_FFT, False), fd, Q1)
+            B.boltz_collide(g.batch(cells, B.BOLTZ_FP32_FFT, False), fd, Q2)
+            B.boltz_stream_status()
+            assert torch.isfinite(Q1).all().item() and torch.equal(Q1, Q2)
+            idx = torch.tensor(list(range(cells))[::-1], dtype=torch.int64, device="cuda")
+            Qi = torch.zeros_like(fd)
+            B.boltz_collide_indexed(g.batch(cells, B.BOLTZ_FP32_FFT, False), fd, Qi, idx, cells)
+            B.boltz_stream_status()
+            assert torch.equal(Qi, Q1)
+    with B.Grid(N, L, 1.0, 8, cluster_size=1, term_groups=2) as g:
+        ft = torch.from_numpy(W.two_maxwellians(1, N, L, seed=173)).cuda()
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_collide(g.batch(1, B.BOLTZ_FP32_FFT), ft, torch.empty_like(ft))
+        assert ei.value.status == B.BOLTZ_EUNSUPPORTED
+
+
 def test_indexed_cells_match_contiguous_batch():
     N, L, M, pool = 16, 6.0, 16, 9
     f = W.two_maxwellians(pool, N, L, seed=61)
