@@ -26,7 +26,10 @@
 //    both pencils' outputs), a CTA barrier, P2 (warp m: the kz pass of plane m), P3 (warp
 //    m: the ky pass of plane m and the gain update in TMEM), a CTA barrier.  Nothing
 //    leaves the SM: no cluster, no distributed shared memory.
-// Twiddles, tables and weights are float32; moments, projection and update float64.
+// Twiddles, tables and weights are float32; moments, projection and update float64, with
+// the float <-> double conversions on the integer pipes (exact, to_f64 / from_f64): with
+// every warp of the SM in the same cell, the float64 phases of a cell do not overlap
+// another cell's float32 work, and the hardware conversions issue to the FP64 pipe.
 #pragma once
 
 #include "collide_kernels.cuh"
@@ -111,12 +114,13 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
       re[y] = (float)p;
       im[y] = (float)q;
       if (args.compute_targets) {
-        s0p += (double)p;
-        s1p += (double)y * (double)p;
-        s2p += (double)(y * y) * (double)p;
-        s0q += (double)q;
-        s1q += (double)y * (double)q;
-        s2q += (double)(y * y) * (double)q;
+        const double pd = to_f64(p), qd = to_f64(q);
+        s0p += pd;
+        s1p += (double)y * pd;
+        s2p += (double)(y * y) * pd;
+        s0q += qd;
+        s1q += (double)y * qd;
+        s2q += (double)(y * y) * qd;
       }
     }
     if (args.compute_targets) {
@@ -212,6 +216,14 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
   const bool doB = doA && !(ky == 0 && kz == 0);
   const int kyB = (N - ky) & (N - 1), kzB = (N - kz) & (N - 1);
   const int mp = warp, zp = lane;             // P2 / P3: plane m = warp; ky (P2) or z (P3) = lane
+  // the first coefficient pair of the next half's P1, loaded before the barrier that
+  // precedes it, so that the L2 latency overlaps the barrier
+  float2 pf[2];
+  {
+    const float2* t0 = tab + (size_t)ky * N * N + kz;
+    pf[0] = __ldg(t0);
+    pf[1] = __ldg(t0 + HN * N);
+  }
   for (int j = 0; j <= M_eff; ++j) {
     const float wj = (j < M_eff) ? (float)args.w[j] : 0.f;
     // coefficients of term j (entry M_eff: (D, 0)) along kx at (ky, kz): tj[kx N]
@@ -233,7 +245,8 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
           for (int q = 0; q < 4; ++q) {
             const int g = 4 * c + q;  // fhat(g) and fhat(g + 16) of A; fhat(16) = 0
             const float f1r = fv[4 * q], f1i = fv[4 * q + 1], f2r = fv[4 * q + 2], f2i = fv[4 * q + 3];
-            const float2 T1 = __ldg(tj + g * N), T2 = __ldg(tj + (g + HN) * N);
+            const float2 T1 = (g == 0) ? pf[0] : __ldg(tj + g * N);
+            const float2 T2 = (g == 0) ? pf[1] : __ldg(tj + (g + HN) * N);
             const float sg = h ? -1.f : 1.f;
             // A at k = g: T1 f1 + (-1)^h T2 f2
             const float uar = T1.x * f1r - T1.y * f1i + sg * (T2.x * f2r - T2.y * f2i);
@@ -334,9 +347,9 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
               const TIO fv = fin[idx];
               const float qv = a16[q] - (float)fv * re[y];
               a16[q] = qv;
-              double gv = args.s * (double)qv;
-              if (args.b != 0.0) gv += args.b * (double)fv;
-              if (fb) gv += args.a * (double)fb[idx];
+              double gv = args.s * to_f64(qv);
+              if (args.b != 0.0) gv += args.b * to_f64(fv);
+              if (fb) gv += args.a * to_f64(fb[idx]);
               S0 += gv;
               S1 += (double)y * gv;
               S2 += (double)(y * y) * gv;
@@ -350,6 +363,11 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
           for (int r = 0; r < 5; ++r) mgs[r * Cfg::THREADS] = (h ? mgs[r * Cfg::THREADS] : 0.0) + m5[r];
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
+      if (!h || j < M_eff) {  // the next half: (j, 1) or (j + 1, 0)
+        const float2* tn = h ? tj + n : tj;
+        pf[0] = __ldg(tn);
+        pf[1] = __ldg(tn + HN * N);
       }
       __syncthreads();  // the planes are read: the next P1 may overwrite them
     }
@@ -392,6 +410,14 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
       c5[r] = s;
     }
   }
+  // R(y) = y (P1 + y P2), the y-part of Phi^T c, the same for every row of the cell:
+  // tabulated once in the (no longer used) warp partials
+  double* Ry = red;
+  if (t < N) {
+    const double P1 = (c5[2] - c5[4] * L) * dv, P2 = 0.5 * c5[4] * dv * dv;
+    Ry[t] = (double)t * (P1 + (double)t * P2);
+  }
+  __syncthreads();
   TIO* out = reinterpret_cast<TIO*>(args.out) + cell * n;
   const TIO* fb = args.f_base ? reinterpret_cast<const TIO*>(args.f_base) + cell * n : nullptr;
   bool bad = false;
@@ -400,10 +426,8 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
     const int x = 2 * mp + h;
     const TIO* fin = cell_input<TIO>(args, cell, x, n);
     const double vx = -L + x * dv, vz = -L + zp * dv;
-    // Phi^T c at (vx, vy, vz) as a quadratic in the row index y: P0 + P1 y + P2 y^2
+    // Phi^T c at (vx, vy, vz) as a quadratic in the row index y: P0 + R(y)
     const double P0 = c5[0] + c5[1] * vx + c5[3] * vz + 0.5 * c5[4] * (vx * vx + vz * vz + L * L) - c5[2] * L;
-    const double P1 = (c5[2] - c5[4] * L) * dv;
-    const double P2 = 0.5 * c5[4] * dv * dv;
     const uint32_t acol = accb + (uint32_t)(h * 32);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -415,12 +439,12 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
         const int y = 16 * c + q;
         const int idx = (x * N + y) * N + zp;
         const TIO fv = fin[idx];
-        double gv = args.s * (double)a16[q];  // the same g as in the sums above
-        if (args.b != 0.0) gv += args.b * (double)fv;
-        if (fb) gv += args.a * (double)fb[idx];
-        const double val = gv + (P0 + (double)y * (P1 + (double)y * P2));
+        double gv = args.s * to_f64(a16[q]);  // the same g as in the sums above
+        if (args.b != 0.0) gv += args.b * to_f64(fv);
+        if (fb) gv += args.a * to_f64(fb[idx]);
+        const double val = gv + (P0 + Ry[y]);
         bad |= !isfinite(val);
-        if (writable) out[idx] = (TIO)val;
+        if (writable) out[idx] = from_f64<TIO>(val);
       }
     }
   }
