@@ -102,10 +102,11 @@ TF32_PER_BF16 = 1.1 / 2.25                            # nominal dense tensor-cor
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as built, on 2048
 # cells (float32 path) and 512 cells (float64 path) of the same workload, divided by the
 # cells of that capture (traffic grows in proportion to the cells: one read of f and one
-# write of the result per cell), keyed by (precision, f stored float64).  None when the
-# kernel or the storage type differs from the capture.
-NCU_DRAM_BYTES_PER_CELL = {("fp32_fft", False): (287.785216e6 + 216.258304e6) / 2048,
-                           ("fp64", True): (176.368896e6 + 97.058304e6) / 512}
+# write of the result per cell), keyed by (kernel, precision, f stored float64): the
+# one-CTA-per-cell kernel of the float32 path and the 8-CTA cluster kernel of the float64
+# path at 32^3.  None when the kernel or the storage type differs from the capture.
+NCU_DRAM_BYTES_PER_CELL = {("collide_solo_kernel", "fp32_fft", False): (281.652224e6 + 209.831168e6) / 2048,
+                           ("collide_kernel", "fp64", True): (176.368896e6 + 97.058304e6) / 512}
 
 
 def algorithmic_flops(N: int, M: int, dim: int = 3) -> float:
@@ -638,7 +639,7 @@ def run_fks(args, wl):
                        "parallelism": f"x-slabs, {ws} GPU(s), ghost exchange per step"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "algorithmic_bytes": 2 * nbytes,
-                         "kernel": "collide_kernel with the transport stage in its loads (one launch per step)",
+                         "kernel": kernel_name(wl, N, 3, grid) + ", the transport stage in its loads",
                          "flops_per_cell": flops_cell},
             "e2e": {"value": cells * ws * e2e_steps / (e2e_ms / 1000.0), "unit": "cell-collisions/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
@@ -778,6 +779,20 @@ def run_targets(args, wl, grid, value, stream) -> dict:
     out["factor_vs_fp64_form"] = value / r64
     del f
     return out
+
+
+def kernel_name(wl, N, dim, grid) -> str:
+    """The collision kernel a launch of this workload runs (one launch per step)."""
+    opts = wl.get("opts", {})
+    if dim == 2:
+        return "collide2d_kernel (one launch per step)"
+    if N in (48, 64) and wl["prec"] == "fp32_fft":
+        return "collide_large_kernel (one launch per step)"
+    cs = opts.get("cluster_size", 0)
+    if (N == 32 and wl["prec"] == "fp32_fft" and int(opts.get("term_groups", 1) or 1) <= 1
+            and (cs == 1 or (cs == 0 and not wl["f64"]))):
+        return "collide_solo_kernel (one CTA per cell, one launch per step)"
+    return "collide_kernel (one launch per step)"
 
 
 def run_ours(args, wl):
@@ -976,11 +991,12 @@ def run_ours(args, wl):
             "config": config_of(args, wl),
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": ((NCU_DRAM_BYTES_PER_CELL.get((wl["prec"], bool(wl["f64"]))) or 0) * cells or None) if dim == 3
+                         "traffic": ((NCU_DRAM_BYTES_PER_CELL.get((kernel_name(wl, N, dim, grid).split()[0], wl["prec"],
+                                                                     bool(wl["f64"]))) or 0) * cells or None) if dim == 3
                          and N == 32 else None,
                          "traffic_unit": "bytes per launch (ncu dram read+write, scaled by cells)",
                          "algorithmic_bytes": 2 * N ** dim * (8 if wl["f64"] else 4) * cells,
-                         "kernel": "collide_kernel (one launch per step)",
+                         "kernel": kernel_name(wl, N, dim, grid),
                          "flops_per_cell": flops_cell, "peak_source": peak_note,
                          "fft_equivalent_tflops": flops_cell * cells / avg_s / 1e12},
             "e2e": {"value": e2e_value, "unit": "cell-collisions/s", "h2d_bytes_per_step": nbytes,

@@ -219,11 +219,16 @@ int default_cluster(int N, int prec) {
     case 8: return 1;
     case 16: return dbl ? 2 : 1;
     case 24: return 3;
-    case 32: return 8;
+    case 32: return dbl ? 8 : 1;  // float32: one CTA per cell (clusters of 8 with term groups)
     case 48: return dbl ? 0 : 12;
     case 64: return dbl ? 0 : 16;
     default: return 0;
   }
+}
+
+int default_cluster_for(int N, int prec, int groups) {
+  const int c = default_cluster(N, prec);
+  return (N == 32 && c == 1 && groups > 1) ? 8 : c;  // the one-CTA-per-cell kernel has no term groups
 }
 
 int cluster_choices(int N, int prec, int* out) {
@@ -239,9 +244,9 @@ int cluster_choices(int N, int prec, int* out) {
       out[k++] = 6;
     }
     if (N == 32) {
+      out[k++] = 8;  // clusters of 8 (also with term groups)
       out[k++] = 4;
       out[k++] = 16;
-      out[k++] = 1;  // one CTA per cell (no term groups)
     }
     if (N == 48) out[k++] = 8;
   }

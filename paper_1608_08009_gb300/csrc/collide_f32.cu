@@ -11,7 +11,10 @@ template <typename T, typename TIO>
 static boltz_status dispatch_n_impl(const boltz_grid_s* g, const CollideArgs& a, int64_t n_cells, cudaStream_t st,
                                int cluster) {
   constexpr bool dbl = sizeof(T) == 8;
-  const int C = cluster > 0 ? cluster : default_cluster(g->N, dbl ? BOLTZ_FP64 : BOLTZ_FP32_FFT);
+  int C = cluster > 0 ? cluster : default_cluster_for(g->N, dbl ? BOLTZ_FP64 : BOLTZ_FP32_FFT, a.groups);
+  // f stored float64 at 32^3: the one-CTA-per-cell kernel spills at its 128 registers
+  // there (float64 loads) and the clusters of 8 measured faster
+  if (cluster <= 0 && sizeof(TIO) == 8 && g->N == 32 && C == 1) C = 8;
   if (g->N == 8 && C == 1) return launch_impl<T, TIO, 8, 1>(a, n_cells, st);
   if constexpr (dbl) {
     if (g->N == 16 && C == 2) return launch_impl<T, TIO, 16, 2>(a, n_cells, st);

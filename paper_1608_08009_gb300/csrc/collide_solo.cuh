@@ -216,6 +216,16 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
   const bool doB = doA && !(ky == 0 && kz == 0);
   const int kyB = (N - ky) & (N - 1), kzB = (N - kz) & (N - 1);
   const int mp = warp, zp = lane;             // P2 / P3: plane m = warp; ky (P2) or z (P3) = lane
+  // g = s Q + b f (+ a f_base, added by the caller) in float64; the usual step (b = 1)
+  // as one fused multiply-add
+  const bool b_one = (args.b == 1.0);
+  auto gval = [&](float qv, TIO fv) -> double {
+    const double qd = to_f64(qv);
+    if (b_one) return fma(args.s, qd, to_f64(fv));
+    double gv = args.s * qd;
+    if (args.b != 0.0) gv += args.b * to_f64(fv);
+    return gv;
+  };
   // the first coefficient pair of the next half's P1, loaded before the barrier that
   // precedes it, so that the L2 latency overlaps the barrier
   float2 pf[2];
@@ -347,8 +357,7 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
               const TIO fv = fin[idx];
               const float qv = a16[q] - (float)fv * re[y];
               a16[q] = qv;
-              double gv = args.s * to_f64(qv);
-              if (args.b != 0.0) gv += args.b * to_f64(fv);
+              double gv = gval(qv, fv);
               if (fb) gv += args.a * to_f64(fb[idx]);
               S0 += gv;
               S1 += (double)y * gv;
@@ -439,8 +448,7 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
         const int y = 16 * c + q;
         const int idx = (x * N + y) * N + zp;
         const TIO fv = fin[idx];
-        double gv = args.s * to_f64(a16[q]);  // the same g as in the sums above
-        if (args.b != 0.0) gv += args.b * to_f64(fv);
+        double gv = gval(a16[q], fv);  // the same g as in the sums above
         if (fb) gv += args.a * to_f64(fb[idx]);
         const double val = gv + (P0 + Ry[y]);
         bad |= !isfinite(val);

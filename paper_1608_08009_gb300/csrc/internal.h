@@ -149,6 +149,9 @@ size_t split_block_bytes(const boltz_grid_s* g, int G, int prec);
 int launch_groups(const boltz_grid_s* g, int prec, int groups);
 // groups < 0: the grid's term_groups; cluster 0: the default cluster size of (N, prec)
 int default_cluster(int N, int prec);
+// The default cluster size of a launch with `groups` term groups (the one-CTA-per-cell
+// 32^3 kernel runs without them; split launches take clusters of 8).
+int default_cluster_for(int N, int prec, int groups);
 // Grow the grid's scratch of split launches (term groups) to n_cells cells of G groups;
 // synchronises `stream` when it has to reallocate.
 boltz_status ensure_split_scratch(const boltz_grid_s* g, int64_t n_cells, int G, int prec, cudaStream_t stream);

@@ -301,7 +301,7 @@ boltz_status boltz_plan_create(const boltz_group* groups, int n_groups, double d
     g.f = groups[i].f;
     g.term_groups = std::max(1, std::min(g.grid->term_groups, g.grid->M_eff));
     g.cluster = (g.prec != BOLTZ_FP64 && g.grid->cluster_size) ? g.grid->cluster_size
-                                                                : boltz::default_cluster(g.grid->N, g.prec);
+                                                                : boltz::default_cluster_for(g.grid->N, g.prec, g.term_groups);
     const size_t n = boltz::cell_points(g.grid);
     const size_t cells = (size_t)std::max<int64_t>(1, g.n_cells);
     if (cudaMalloc(&g.U0, cells * 5 * sizeof(double)) != cudaSuccess ||
