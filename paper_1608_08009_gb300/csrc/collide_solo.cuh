@@ -219,6 +219,10 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
   // g = s Q + b f (+ a f_base, added by the caller) in float64; the usual step (b = 1)
   // as one fused multiply-add
   const bool b_one = (args.b == 1.0);
+  // With the targets computed here (Phi f_in summed by the forward pass) and no f_base,
+  // Phi g = s Phi Q + b Phi f_in: the loss pass then sums Q alone, one float64 operation a
+  // point fewer
+  const bool q_sums = args.compute_targets && !args.f_base;
   auto gval = [&](float qv, TIO fv) -> double {
     const double qd = to_f64(qv);
     if (b_one) return fma(args.s, qd, to_f64(fv));
@@ -357,8 +361,13 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
               const TIO fv = fin[idx];
               const float qv = a16[q] - (float)fv * re[y];
               a16[q] = qv;
-              double gv = gval(qv, fv);
-              if (fb) gv += args.a * to_f64(fb[idx]);
+              double gv;
+              if (q_sums) {
+                gv = to_f64(qv);
+              } else {
+                gv = gval(qv, fv);
+                if (fb) gv += args.a * to_f64(fb[idx]);
+              }
               S0 += gv;
               S1 += (double)y * gv;
               S2 += (double)(y * y) * gv;
@@ -397,11 +406,14 @@ __global__ void __launch_bounds__(SoloCfg::THREADS, 1) collide_solo_kernel(const
   __syncthreads();
   double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (args.project) {
-    const double* tot = red + WARPS * 10;
+    const double* sums = red + WARPS * 10;
+    double tot[5];  // Phi g
+#pragma unroll
+    for (int r = 0; r < 5; ++r) tot[r] = q_sums ? args.s * sums[r] + args.b * sums[5 + r] : sums[r];
     double tgt[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (args.compute_targets) {
 #pragma unroll
-      for (int r = 0; r < 5; ++r) tgt[r] = tot[5 + r];
+      for (int r = 0; r < 5; ++r) tgt[r] = sums[5 + r];
       if (args.Utgt && writable) {
 #pragma unroll
         for (int r = 0; r < 5; ++r)
