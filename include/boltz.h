@@ -95,12 +95,17 @@ typedef struct {
                         kept with the grid).  Clamped to [1, M_eff].  Results depend on G (rounding
                         order of the gain sum) but not on the batch size.               */
   int cluster_size;  /* thread-block cluster size (CTAs per cell) of the float32 path;
-                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 8, 48: 12, 64: 16).  Also
-                        built: 16: 2, 4; 24: 2, 6; 32: 4, 16; 48: 8.  Larger clusters give each CTA
-                        a thinner slab (fewer threads, more CTAs per SM).  The float64
-                        path always uses its own size (8: 1, 16: 2, 24: 3, 32: 8).
-                        Results agree across sizes up to the rounding of the moment sums
-                        (summed per CTA, then across the cluster).  Other values:
+                        0 = default (N 8: 1, 16: 1, 24: 3, 32: 1, 48: 12, 64: 16).  Also
+                        built: 16: 2, 4; 24: 2, 6; 32: 8, 4, 16; 48: 8.  Larger clusters give
+                        each CTA a thinner slab (fewer threads, more CTAs per SM).  At N = 32
+                        size 1 is one 512-thread CTA per cell that holds half the spectrum
+                        and the gain in tensor memory and runs each inverse transform in two
+                        halves of x; it takes no term groups (with term_groups > 1 the
+                        default becomes 8, an explicit 1 returns BOLTZ_EUNSUPPORTED) and, by
+                        default, is not used for f stored in float64 (clusters of 8 there).
+                        The float64 path always uses its own size (8: 1, 16: 2, 24: 3,
+                        32: 8).  Results agree across sizes up to float32 rounding (transform
+                        order) and the rounding of the moment sums.  Other values:
                         BOLTZ_EUNSUPPORTED. */
 } boltz_grid_opts;
 
